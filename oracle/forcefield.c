@@ -1,0 +1,269 @@
+/*
+ * FP64 oracle: energy and analytic gradient of the OPLS-style potential of
+ * arXiv 1810.03358, Section 2 (TEST INFRASTRUCTURE ONLY, see ffmin_oracle.h).
+ *
+ *   E = E_stretch + E_bend + E_torsion + E_cul + E_vdw           (Section 2)
+ *   E_stretch = sum_bonds K (r - r0)^2                            (no 1/2)
+ *   E_bend    = sum_angles K_theta (theta - theta0)^2             (no 1/2)
+ *   E_torsion = sum_dihedrals 1/2 [V1(1+cos phi) + V2(1-cos 2phi)
+ *                                  + V3(1+cos 3phi) + V4(1-cos 4phi)]
+ *   E_cul     = C sum_{i<j} q_i q_j / r_ij
+ *   E_vdw     = 4 sum_{i<j} sqrt(eps_i eps_j) [(s/r)^12 - (s/r)^6],
+ *               s = sqrt(sigma_i sigma_j)
+ * Pairs run over ALL i < j: the paper's non-bonded forces act regardless of
+ * whether a bond joins the atoms, so there is no exclusion list.
+ * Gradients are the explicit formulas (Section 2 prefers them to autodiff).
+ */
+#include "ffmin_oracle.h"
+
+#include <math.h>
+#include <stddef.h>
+
+static void sub3(const double *a, const double *b, double *o) {
+    o[0] = a[0] - b[0]; o[1] = a[1] - b[1]; o[2] = a[2] - b[2];
+}
+static double dot3(const double *a, const double *b) {
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+static void cross3(const double *a, const double *b, double *o) {
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+/* Pair term between atoms with the given parameters at separation vector
+ * d = x_i - x_j.  Returns E_cul + E_vdw of the pair; *ec, *ev the parts;
+ * *dedr_over_r = (dE/dr)/r so that grad_i = dedr_over_r * d. */
+static double pair_term(double c, double qi, double qj, double si, double sj,
+                        double ei, double ej, const double *d,
+                        double *ec, double *ev, double *dedr_over_r) {
+    double r2 = dot3(d, d);
+    double r = sqrt(r2);
+    double sij = sqrt(si * sj);
+    double eij = sqrt(ei * ej);
+    double sr = sij / r;
+    double sr6 = pow(sr, 6.0);
+    double sr12 = sr6 * sr6;
+    *ec = c * qi * qj / r;
+    *ev = 4.0 * eij * (sr12 - sr6);
+    /* dE_cul/dr = -C qi qj / r^2 ; dE_vdw/dr = 4 eps (-12 sr^12 + 6 sr^6) / r */
+    double dcul = -(*ec) / r;
+    double dvdw = 4.0 * eij * (-12.0 * sr12 + 6.0 * sr6) / r;
+    *dedr_over_r = (dcul + dvdw) / r;
+    return *ec + *ev;
+}
+
+/* Bond i-j: E = K (r - r0)^2; grad_i = 2K (r - r0) (x_i - x_j)/r. */
+static double bond_term(const double *xi, const double *xj, double k, double r0,
+                        double *gi, double *gj) {
+    double d[3];
+    sub3(xi, xj, d);
+    double r = sqrt(dot3(d, d));
+    double e = k * (r - r0) * (r - r0);
+    if (gi) {
+        double f = 2.0 * k * (r - r0) / r;
+        for (int a = 0; a < 3; a++) { gi[a] = f * d[a]; gj[a] = -f * d[a]; }
+    }
+    return e;
+}
+
+/* Angle i-j-k (vertex j): theta = atan2(|u x v|, u.v), u = x_i - x_j,
+ * v = x_k - x_j; E = K (theta - theta0)^2.
+ * d theta/d x_i = [(u.v) u/|u|^2 - v] / |u x v|, likewise for x_k with u, v
+ * swapped; d theta/d x_j = -(d/dx_i + d/dx_k).  At |u x v| = 0 the angle is
+ * not differentiable; the gradient contribution is then taken as zero. */
+static double angle_term(const double *xi, const double *xj, const double *xk,
+                         double kth, double th0, double *gi, double *gj, double *gk) {
+    double u[3], v[3], w[3];
+    sub3(xi, xj, u);
+    sub3(xk, xj, v);
+    cross3(u, v, w);
+    double cr = sqrt(dot3(w, w));
+    double uv = dot3(u, v);
+    double th = atan2(cr, uv);
+    double e = kth * (th - th0) * (th - th0);
+    if (gi) {
+        if (cr > 0.0) {
+            double de = 2.0 * kth * (th - th0);
+            double uu = dot3(u, u), vv = dot3(v, v);
+            for (int a = 0; a < 3; a++) {
+                double dti = (uv * u[a] / uu - v[a]) / cr;
+                double dtk = (uv * v[a] / vv - u[a]) / cr;
+                gi[a] = de * dti;
+                gk[a] = de * dtk;
+                gj[a] = -(gi[a] + gk[a]);
+            }
+        } else {
+            for (int a = 0; a < 3; a++) { gi[a] = 0.0; gj[a] = 0.0; gk[a] = 0.0; }
+        }
+    }
+    return e;
+}
+
+/* Dihedral i-j-k-l: b1 = x_j - x_i, b2 = x_k - x_j, b3 = x_l - x_k,
+ * m = b1 x b2, n = b2 x b3, phi = atan2(|b2| b1.n, m.n) (cis = 0,
+ * trans = pi).  E = 1/2 [V1(1+cos phi) + V2(1-cos 2phi) + V3(1+cos 3phi)
+ * + V4(1-cos 4phi)].  Gradient of phi (Blondel & Karplus 1996):
+ *   dphi/dx_i = -|b2|/|m|^2 m,  dphi/dx_l = |b2|/|n|^2 n,
+ *   dphi/dx_j = -(1 + a) dphi/dx_i + c dphi/dx_l,
+ *   dphi/dx_k = a dphi/dx_i - (1 + c) dphi/dx_l,
+ * with a = b1.b2/|b2|^2 and c = b3.b2/|b2|^2.  When |m|^2 or |n|^2 falls
+ * below 1e-12 A^4 (collinear atoms) phi is taken from atan2 as is and the
+ * gradient contribution is zero. */
+static double dihedral_term(const double *xi, const double *xj, const double *xk,
+                            const double *xl, const double *v, double *gi, double *gj,
+                            double *gk, double *gl, int *degenerate) {
+    double b1[3], b2[3], b3[3], m[3], n[3];
+    sub3(xj, xi, b1);
+    sub3(xk, xj, b2);
+    sub3(xl, xk, b3);
+    cross3(b1, b2, m);
+    cross3(b2, b3, n);
+    double mm = dot3(m, m), nn = dot3(n, n), b2n = sqrt(dot3(b2, b2));
+    double phi = atan2(b2n * dot3(b1, n), dot3(m, n));
+    double e = 0.5 * (v[0] * (1.0 + cos(phi)) + v[1] * (1.0 - cos(2.0 * phi)) +
+                      v[2] * (1.0 + cos(3.0 * phi)) + v[3] * (1.0 - cos(4.0 * phi)));
+    int deg = (mm < 1e-12 || nn < 1e-12);
+    if (degenerate) *degenerate = deg;
+    if (gi) {
+        if (deg) {
+            for (int a = 0; a < 3; a++) { gi[a] = gj[a] = gk[a] = gl[a] = 0.0; }
+        } else {
+            double dedphi = 0.5 * (-v[0] * sin(phi) + 2.0 * v[1] * sin(2.0 * phi) -
+                                   3.0 * v[2] * sin(3.0 * phi) + 4.0 * v[3] * sin(4.0 * phi));
+            double bb = b2n * b2n;
+            double ca = dot3(b1, b2) / bb, cc = dot3(b3, b2) / bb;
+            for (int a = 0; a < 3; a++) {
+                double pi_ = -b2n / mm * m[a];
+                double pl = b2n / nn * n[a];
+                double pj = -(1.0 + ca) * pi_ + cc * pl;
+                double pk = ca * pi_ - (1.0 + cc) * pl;
+                gi[a] = dedphi * pi_;
+                gj[a] = dedphi * pj;
+                gk[a] = dedphi * pk;
+                gl[a] = dedphi * pl;
+            }
+        }
+    }
+    return e;
+}
+
+int orc_energy_terms(const orc_ff *ff, const double *x, double *grad, orc_terms *out) {
+    const int n = ff->n_atoms;
+    orc_terms t = {0};
+    int status = ORC_OK;
+    if (grad)
+        for (int k = 0; k < 3 * n; k++) grad[k] = 0.0;
+
+    /* non-bonded: every unordered pair i < j */
+    for (int i = 0; i < n; i++) {
+        for (int j = i + 1; j < n; j++) {
+            double d[3];
+            sub3(x + 3 * i, x + 3 * j, d);
+            if (dot3(d, d) == 0.0) { status = ORC_NONFINITE; continue; }
+            double ec, ev, f;
+            pair_term(ff->coulomb_c, ff->charge[i], ff->charge[j], ff->sigma[i], ff->sigma[j],
+                      ff->epsilon[i], ff->epsilon[j], d, &ec, &ev, &f);
+            t.coulomb += ec;
+            t.vdw += ev;
+            t.sum_abs += fabs(ec) + fabs(ev);
+            if (grad) {
+                for (int a = 0; a < 3; a++) {
+                    grad[3 * i + a] += f * d[a];
+                    grad[3 * j + a] -= f * d[a];
+                }
+            }
+        }
+    }
+    /* bonds */
+    for (int b = 0; b < ff->n_bonds; b++) {
+        int i = ff->bond_idx[2 * b], j = ff->bond_idx[2 * b + 1];
+        double gi[3], gj[3];
+        double e = bond_term(x + 3 * i, x + 3 * j, ff->bond_k[b], ff->bond_r0[b],
+                             grad ? gi : NULL, gj);
+        t.stretch += e;
+        t.sum_abs += fabs(e);
+        if (grad)
+            for (int a = 0; a < 3; a++) { grad[3 * i + a] += gi[a]; grad[3 * j + a] += gj[a]; }
+    }
+    /* angles */
+    for (int b = 0; b < ff->n_angles; b++) {
+        int i = ff->angle_idx[3 * b], j = ff->angle_idx[3 * b + 1], k = ff->angle_idx[3 * b + 2];
+        double gi[3], gj[3], gk[3];
+        double e = angle_term(x + 3 * i, x + 3 * j, x + 3 * k, ff->angle_k[b],
+                              ff->angle_theta0[b], grad ? gi : NULL, gj, gk);
+        t.bend += e;
+        t.sum_abs += fabs(e);
+        if (grad)
+            for (int a = 0; a < 3; a++) {
+                grad[3 * i + a] += gi[a]; grad[3 * j + a] += gj[a]; grad[3 * k + a] += gk[a];
+            }
+    }
+    /* dihedrals */
+    for (int b = 0; b < ff->n_dihedrals; b++) {
+        const int32_t *q = ff->dihedral_idx + 4 * b;
+        double gi[3], gj[3], gk[3], gl[3];
+        int deg = 0;
+        double e = dihedral_term(x + 3 * q[0], x + 3 * q[1], x + 3 * q[2], x + 3 * q[3],
+                                 ff->dihedral_v + 4 * b, grad ? gi : NULL, gj, gk, gl, &deg);
+        t.torsion += e;
+        t.sum_abs += fabs(e);
+        t.degenerate_dihedrals += deg;
+        if (grad)
+            for (int a = 0; a < 3; a++) {
+                grad[3 * q[0] + a] += gi[a]; grad[3 * q[1] + a] += gj[a];
+                grad[3 * q[2] + a] += gk[a]; grad[3 * q[3] + a] += gl[a];
+            }
+    }
+    t.total = t.stretch + t.bend + t.torsion + t.coulomb + t.vdw;
+    if (!isfinite(t.total)) status = ORC_NONFINITE;
+    if (grad)
+        for (int k = 0; k < 3 * n; k++)
+            if (!isfinite(grad[k])) status = ORC_NONFINITE;
+    if (out) *out = t;
+    return status;
+}
+
+/* Part of E that depends on atom i, with atom i at p. */
+double orc_row_energy(const orc_ff *ff, const double *x, int32_t i, const double p[3]) {
+    const int n = ff->n_atoms;
+    double e = 0.0;
+    for (int j = 0; j < n; j++) {
+        if (j == i) continue;
+        double d[3], ec, ev, f;
+        sub3(p, x + 3 * j, d);
+        e += pair_term(ff->coulomb_c, ff->charge[i], ff->charge[j], ff->sigma[i], ff->sigma[j],
+                       ff->epsilon[i], ff->epsilon[j], d, &ec, &ev, &f);
+    }
+#define POS(a) ((a) == i ? p : x + 3 * (a))
+    for (int b = 0; b < ff->n_bonds; b++) {
+        int a0 = ff->bond_idx[2 * b], a1 = ff->bond_idx[2 * b + 1];
+        if (a0 != i && a1 != i) continue;
+        e += bond_term(POS(a0), POS(a1), ff->bond_k[b], ff->bond_r0[b], NULL, NULL);
+    }
+    for (int b = 0; b < ff->n_angles; b++) {
+        const int32_t *q = ff->angle_idx + 3 * b;
+        if (q[0] != i && q[1] != i && q[2] != i) continue;
+        e += angle_term(POS(q[0]), POS(q[1]), POS(q[2]), ff->angle_k[b], ff->angle_theta0[b],
+                        NULL, NULL, NULL);
+    }
+    for (int b = 0; b < ff->n_dihedrals; b++) {
+        const int32_t *q = ff->dihedral_idx + 4 * b;
+        if (q[0] != i && q[1] != i && q[2] != i && q[3] != i) continue;
+        e += dihedral_term(POS(q[0]), POS(q[1]), POS(q[2]), POS(q[3]), ff->dihedral_v + 4 * b,
+                           NULL, NULL, NULL, NULL, NULL);
+    }
+#undef POS
+    return e;
+}
+
+int32_t orc_neighbour_count(const orc_ff *ff, const double *x, int32_t i, double rc) {
+    int32_t c = 0;
+    for (int j = 0; j < ff->n_atoms; j++) {
+        if (j == i) continue;
+        double d[3];
+        sub3(x + 3 * i, x + 3 * j, d);
+        if (dot3(d, d) < rc * rc) c++;
+    }
+    return c;
+}

@@ -1,0 +1,574 @@
+/*
+ * FP64 oracle: line searches and minimizers of arXiv 1810.03358
+ * (TEST INFRASTRUCTURE ONLY, see ffmin_oracle.h).
+ *
+ *   LS_H    Algorithm 5 (Section 5.2)
+ *   LS_PAR  Algorithm 6 (Section 5.2)
+ *   GD      adaptive steepest descent, Eq. 4, step from LS_PAR (Section 3)
+ *   FGM     Algorithm 1 (Section 5.1)
+ *   CG      Algorithm 2, beta variants of Section 4 / Section 5.1
+ *   L-BFGS  Algorithms 3 and 4 (Section 5.1)
+ *   parab   gradient-free random-atom moves (Section 3)
+ *
+ * Readings where the paper is silent (also listed in the design notes):
+ *  - every search direction is normalised to unit 2-norm before the line
+ *    search (Section 5.1), so h is the 2-norm of the step;
+ *  - the step accepted in one search is the next search's h0 (Section 5.2);
+ *  - a failed search restarts the method once from the antigradient with
+ *    momentum / history cleared and h0 reset; a second consecutive failure
+ *    stops with ORC_LINESEARCH (Section 5.1: stop or change direction);
+ *  - convergence: max_k |dE/dx_k| < gtol_inf after a gradient evaluation;
+ *  - LS_PAR with K = 2 runs the refinement loop once (3 evaluations);
+ *    degenerate parabolas (curvature <= 0, non-finite vertex) step to
+ *    k_plus times the best non-zero step (half the smallest step when the
+ *    best point is h = 0); a refined vertex is clamped to 8 x max|h|;
+ *  - a non-finite trial energy counts as +inf inside a line search;
+ *  - L-BFGS scales H0 by <s,y>/<y,y> of the newest stored pair and skips
+ *    pairs with <s,y> <= 0;
+ *  - CG: beta uses the previous unnormalised direction; restart every
+ *    cg_restart_every iterations and whenever <g+, r+> >= 0;
+ *  - FGM: stop when |grad f(w)|_inf < tol and return the better of the best
+ *    iterate and w; the momentum is reset (theta <- 1, x^{k-1} <- x^{k+1})
+ *    whenever f(x^{k+1}) > f(x^k), the function-value adaptive restart of
+ *    O'Donoghue and Candes that Section 4 cites for restarting.
+ * A trial point x + h r is formed as fma(h, r_k, x_k) per component.
+ */
+#include "ffmin_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---------------- trace of the last run ---------------- */
+#define TRACE_CAP 200000
+static double tr_f[TRACE_CAP], tr_h[TRACE_CAP], tr_th[TRACE_CAP], tr_b[TRACE_CAP];
+static int32_t tr_n;
+static void trace_reset(void) { tr_n = 0; }
+static void trace_add(double f, double h, double th, double b) {
+    if (tr_n < TRACE_CAP) {
+        tr_f[tr_n] = f; tr_h[tr_n] = h; tr_th[tr_n] = th; tr_b[tr_n] = b; tr_n++;
+    }
+}
+int32_t orc_trace(double *f, double *h, double *theta, double *beta, int32_t cap) {
+    int32_t n = tr_n < cap ? tr_n : cap;
+    for (int32_t k = 0; k < n; k++) {
+        if (f) f[k] = tr_f[k];
+        if (h) h[k] = tr_h[k];
+        if (theta) theta[k] = tr_th[k];
+        if (beta) beta[k] = tr_b[k];
+    }
+    return n;
+}
+
+/* ---------------- SplitMix64 ---------------- */
+uint64_t orc_splitmix64(uint64_t seed, uint64_t k) {
+    uint64_t z = seed + (k + 1) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+int32_t orc_pick_atom(uint64_t seed, uint64_t k, int32_t n) {
+    unsigned __int128 p = (unsigned __int128)orc_splitmix64(seed, k) * (uint64_t)n;
+    return (int32_t)(p >> 64);
+}
+
+void orc_options_default(orc_options *o) {
+    memset(o, 0, sizeof(*o));
+    o->method = ORC_LBFGS;
+    o->cg_variant = ORC_CG_PRP;
+    o->ls = ORC_LS_DEFAULT;
+    o->lbfgs_m = 10;
+    o->gtol_inf = 0.1;
+    o->max_iter = 100000;
+    o->max_evals = 1000000;
+    o->cg_restart_every = 0; /* 0 -> number of variables */
+    o->h0 = 0.1;
+    o->k_plus = 2.0;
+    o->k_minus = 0.5;
+    o->eps_h = 1e-10;
+    o->ls_par_K = 2;
+    o->ls_par_g0 = 1;
+    o->gradfree_delta = 0.05;
+    o->seed = 12345;
+    o->precond_d = NULL;
+}
+
+static double finite_or_inf(double f) { return isfinite(f) ? f : HUGE_VAL; }
+
+/* ---------------- LS_H (Algorithm 5) ---------------- */
+double orc_ls_h(orc_line_fn phi, void *ctx, double f_star, double h0, double eps_h,
+                double k_plus, double k_minus, double *f_out, int32_t *n_evals) {
+    int32_t ne = 0;
+    double f0 = finite_or_inf(phi(ctx, h0)); ne++;
+    if (f0 < f_star) {
+        double h1 = k_plus * h0;
+        double f1 = finite_or_inf(phi(ctx, h1)); ne++;
+        *n_evals = ne;
+        if (f1 < f0) { *f_out = f1; return h1; }
+        *f_out = f0;
+        return h0;
+    }
+    double h2 = k_minus * h0;
+    double f2 = finite_or_inf(phi(ctx, h2)); ne++;
+    while (f2 > f_star) {
+        h2 = k_minus * h2;
+        if (h2 <= eps_h) { *n_evals = ne; *f_out = f_star; return 0.0; }
+        f2 = finite_or_inf(phi(ctx, h2)); ne++;
+    }
+    *n_evals = ne;
+    *f_out = f2;
+    return h2;
+}
+
+/* ---------------- LS_PAR (Algorithm 6) ---------------- */
+/* Vertex of the parabola through three points (Newton form
+ * p(h) = f0 + d1 (h - h0) + A (h - h0)(h - h1)); returns 0 when the
+ * curvature A is not positive or the vertex is not finite. */
+static int parabola3(const double *h, const double *f, double *vertex) {
+    double d1 = (f[1] - f[0]) / (h[1] - h[0]);
+    double d2 = (f[2] - f[1]) / (h[2] - h[1]);
+    double A = (d2 - d1) / (h[2] - h[0]);
+    if (!(A > 0.0) || !isfinite(A)) return 0;
+    double v = 0.5 * (h[0] + h[1]) - d1 / (2.0 * A);
+    if (!isfinite(v)) return 0;
+    *vertex = v;
+    return 1;
+}
+
+/* order two points: by f ascending, then by |h| ascending */
+static int point_less(double ha, double fa, double hb, double fb) {
+    if (fa < fb) return 1;
+    if (fa > fb) return 0;
+    return fabs(ha) < fabs(hb);
+}
+
+static void sort_points(double *h, double *f, int n) {
+    for (int a = 1; a < n; a++) { /* insertion sort, stable */
+        double hh = h[a], ff = f[a];
+        int b = a - 1;
+        while (b >= 0 && point_less(hh, ff, h[b], f[b])) {
+            h[b + 1] = h[b]; f[b + 1] = f[b]; b--;
+        }
+        h[b + 1] = hh; f[b + 1] = ff;
+    }
+}
+
+double orc_ls_par(orc_line_fn phi, void *ctx, double f_star, double slope, double h0,
+                  int32_t K, int32_t g0, double k_plus, double *f_out, int32_t *n_evals) {
+    int32_t ne = 0;
+    double h[4], f[4];
+    h[0] = 0.0; f[0] = f_star;
+    if (g0) {
+        h[1] = h0;
+        f[1] = finite_or_inf(phi(ctx, h[1])); ne++;
+        /* parabola through f(0) = f*, f'(0) = slope and (h1, f1) */
+        double a = (f[1] - f_star - slope * h[1]) / (h[1] * h[1]);
+        double v = -slope / (2.0 * a);
+        if (a > 0.0 && isfinite(a) && isfinite(v)) h[2] = v;
+        else h[2] = k_plus * h[1];
+        f[2] = finite_or_inf(phi(ctx, h[2])); ne++;
+    } else {
+        h[1] = -0.5 * h0;
+        f[1] = finite_or_inf(phi(ctx, h[1])); ne++;
+        h[2] = 0.5 * h0;
+        f[2] = finite_or_inf(phi(ctx, h[2])); ne++;
+    }
+    for (int32_t k = 2; k <= K; k++) {
+        double v;
+        double hmax = fmax(fabs(h[0]), fmax(fabs(h[1]), fabs(h[2])));
+        if (!parabola3(h, f, &v)) {
+            /* degenerate: step beyond the best non-zero point, or back
+             * towards 0 when h = 0 is the best point */
+            int ib = 0;
+            for (int a = 1; a < 3; a++)
+                if (point_less(h[a], f[a], h[ib], f[ib])) ib = a;
+            if (h[ib] != 0.0) {
+                v = k_plus * h[ib];
+            } else {
+                int ic = -1;
+                for (int a = 0; a < 3; a++)
+                    if (h[a] != 0.0 && (ic < 0 || fabs(h[a]) < fabs(h[ic]))) ic = a;
+                v = ic >= 0 ? 0.5 * h[ic] : h0;
+            }
+        }
+        if (fabs(v) > 8.0 * hmax) v = copysign(8.0 * hmax, v);
+        h[3] = v;
+        f[3] = finite_or_inf(phi(ctx, h[3])); ne++;
+        sort_points(h, f, 4);
+    }
+    if (K == 2) sort_points(h, f, 3); /* the paper's extra sort; already sorted */
+    *n_evals = ne;
+    if (f[0] < f_star) { *f_out = f[0]; return h[0]; }
+    *f_out = f_star;
+    return 0.0;
+}
+
+/* ---------------- minimizers ---------------- */
+typedef struct {
+    int32_t n;
+    orc_fg_fn fg;
+    void *ctx;
+    int32_t ne, neg;
+    int32_t status;
+} obj_t;
+
+static double obj_e(obj_t *o, const double *x) {
+    int32_t st = 0;
+    double f = o->fg(o->ctx, x, NULL, &st);
+    o->ne++;
+    if (st) return INFINITY;
+    return f;
+}
+static double obj_eg(obj_t *o, const double *x, double *g) {
+    int32_t st = 0;
+    double f = o->fg(o->ctx, x, g, &st);
+    o->neg++;
+    if (st || !isfinite(f)) o->status = ORC_NONFINITE;
+    return f;
+}
+
+typedef struct {
+    obj_t *o;
+    const double *x, *r;
+    double *xt;
+} line_t;
+
+static double line_phi(void *ctx, double h) {
+    line_t *l = (line_t *)ctx;
+    for (int32_t k = 0; k < l->o->n; k++) l->xt[k] = fma(h, l->r[k], l->x[k]);
+    return obj_e(l->o, l->xt);
+}
+
+static double dotn(int32_t n, const double *a, const double *b) {
+    double s = 0.0;
+    for (int32_t k = 0; k < n; k++) s += a[k] * b[k];
+    return s;
+}
+static double infnorm(int32_t n, const double *a) {
+    double m = 0.0;
+    for (int32_t k = 0; k < n; k++) m = fmax(m, fabs(a[k]));
+    return m;
+}
+
+/* direction normalisation (Section 5.1): rhat = r * (1/|r|_2) */
+static void normalise(int32_t n, const double *r, double *rhat) {
+    double inv = 1.0 / sqrt(dotn(n, r, r));
+    for (int32_t k = 0; k < n; k++) rhat[k] = r[k] * inv;
+}
+
+static double line_search(const orc_options *op, int method, obj_t *o, const double *x,
+                          const double *rhat, double *xt, double f_star, double slope,
+                          double h0, double *f_out, int32_t *ne) {
+    line_t l = {o, x, rhat, xt};
+    int ls = op->ls;
+    if (ls == ORC_LS_DEFAULT) ls = (method == ORC_FGM) ? ORC_LS_H : ORC_LS_PAR;
+    if (ls == ORC_LS_H)
+        return orc_ls_h(line_phi, &l, f_star, h0, op->eps_h, op->k_plus, op->k_minus, f_out, ne);
+    return orc_ls_par(line_phi, &l, f_star, slope, h0, op->ls_par_K, op->ls_par_g0,
+                      op->k_plus, f_out, ne);
+}
+
+/* L-BFGS two-loop recursion, Algorithm 3 (readings: scale by the newest
+ * pair; loops over the stored pairs; optional H0 diagonal d). */
+void orc_lbfgs_direction(int32_t n, const double *g, int32_t count, const double *s,
+                         const double *y, const double *d, double *r) {
+    for (int32_t k = 0; k < n; k++) r[k] = -g[k];
+    if (count == 0) return;
+    double *alpha = (double *)malloc(sizeof(double) * count);
+    double *rho = (double *)malloc(sizeof(double) * count);
+    for (int32_t i = 0; i < count; i++) rho[i] = 1.0 / dotn(n, s + (size_t)i * n, y + (size_t)i * n);
+    for (int32_t i = count - 1; i >= 0; i--) { /* newest -> oldest */
+        const double *si = s + (size_t)i * n, *yi = y + (size_t)i * n;
+        alpha[i] = rho[i] * dotn(n, si, r);
+        for (int32_t k = 0; k < n; k++) r[k] -= alpha[i] * yi[k];
+    }
+    const double *sn = s + (size_t)(count - 1) * n, *yn = y + (size_t)(count - 1) * n;
+    double gamma = dotn(n, sn, yn) / dotn(n, yn, yn);
+    for (int32_t k = 0; k < n; k++) r[k] = d ? gamma * d[k] * r[k] : gamma * r[k];
+    for (int32_t i = 0; i < count; i++) { /* oldest -> newest */
+        const double *si = s + (size_t)i * n, *yi = y + (size_t)i * n;
+        double beta = rho[i] * dotn(n, yi, r);
+        for (int32_t k = 0; k < n; k++) r[k] += (alpha[i] - beta) * si[k];
+    }
+    free(alpha);
+    free(rho);
+}
+
+static double cg_beta(int variant, int32_t n, const double *gp, const double *g,
+                      const double *d) {
+    /* y = g+ - g ; d = previous unnormalised direction */
+    double gpy = 0.0, dy = 0.0, gpgp = dotn(n, gp, gp), gg = dotn(n, g, g), dg = dotn(n, d, g);
+    for (int32_t k = 0; k < n; k++) {
+        double yk = gp[k] - g[k];
+        gpy += gp[k] * yk;
+        dy += d[k] * yk;
+    }
+    switch (variant) {
+    case ORC_CG_HS: return gpy / dy;
+    case ORC_CG_FR: return gpgp / gg;
+    case ORC_CG_PRP_PLUS: return fmax(0.0, gpy / gg);
+    case ORC_CG_CD: return gpgp / (-dg);
+    case ORC_CG_LS: return gpy / (-dg);
+    case ORC_CG_DY: return gpgp / dy;
+    case ORC_CG_PRP:
+    default: return gpy / gg;
+    }
+}
+
+#define CAP_HIT(it, o) ((it) >= op->max_iter || (o).ne + (o).neg >= op->max_evals)
+
+int orc_minimize(int32_t n, orc_fg_fn fg, void *ctx, double *x, const orc_options *op,
+                 orc_result *res) {
+    obj_t o = {n, fg, ctx, 0, 0, ORC_OK};
+    int method = op->method;
+    trace_reset();
+    memset(res, 0, sizeof(*res));
+    if (method == ORC_GRADFREE) { res->status = ORC_BAD_ARG; return ORC_BAD_ARG; }
+    size_t nb = sizeof(double) * (size_t)n;
+    double *g = malloc(nb), *r = malloc(nb), *rhat = malloc(nb), *xt = malloc(nb),
+           *gn = malloc(nb), *xn = malloc(nb), *xp = malloc(nb), *xb = malloc(nb);
+    int m = op->lbfgs_m > 0 ? op->lbfgs_m : 1;
+    double *S = malloc(nb * m), *Y = malloc(nb * m);
+    int32_t hist = 0;
+    int32_t restart_every = op->cg_restart_every > 0 ? op->cg_restart_every : n;
+    int status = ORC_OK;
+    int32_t it = 0, lsf = 0;
+    double h0 = op->h0;
+    int fresh = 1;
+    double f = obj_eg(&o, x, g);
+    double ginf = infnorm(n, g);
+    double result_f = f, result_ginf = ginf;
+    if (o.status) { status = o.status; goto done; }
+
+    if (method == ORC_FGM) {
+        /* Algorithm 1: x_* <- x0, x^{-1} <- x0, theta_{-1} <- 1 */
+        double th_prev = 1.0, fb = f, fw = f, fx = f;
+        memcpy(xp, x, nb);
+        memcpy(xb, x, nb);
+        double *w = xn, *gw = gn;
+        memcpy(w, x, nb);
+        memcpy(gw, g, nb);
+        int have_w = 1; /* w^0 = x^0: its E and gradient are already known */
+        int xb_is_w_grad = 1; /* gradient at xb known (= gw) */
+        double xb_ginf = ginf;
+        for (;;) {
+            double th = 0.5 * th_prev * (sqrt(th_prev * th_prev + 4.0) - th_prev);
+            double beta = th_prev * (1.0 - th_prev) / (th_prev * th_prev + th);
+            if (!have_w) {
+                for (int32_t k = 0; k < n; k++) w[k] = fma(beta, x[k] - xp[k], x[k]);
+                fw = obj_eg(&o, w, gw);
+                if (o.status) { status = o.status; break; }
+            }
+            have_w = 0;
+            double gwinf = infnorm(n, gw);
+            if (gwinf < op->gtol_inf) {
+                if (fw < fb) { memcpy(xb, w, nb); fb = fw; xb_ginf = gwinf; xb_is_w_grad = 1; }
+                status = ORC_OK;
+                break;
+            }
+            if (CAP_HIT(it, o)) { status = ORC_MAX_ITER; break; }
+            for (int32_t k = 0; k < n; k++) r[k] = -gw[k];
+            normalise(n, r, rhat);
+            int32_t ne = 0;
+            double fnew;
+            double h = line_search(op, method, &o, w, rhat, xt, fw, dotn(n, gw, rhat), h0, &fnew, &ne);
+            if (h == 0.0) {
+                lsf++;
+                if (fresh) { status = ORC_LINESEARCH; break; }
+                fresh = 1;
+                th_prev = 1.0;
+                memcpy(x, w, nb);
+                memcpy(xp, w, nb);
+                fx = fw;
+                h0 = op->h0;
+                continue;
+            }
+            fresh = 0;
+            memcpy(xp, x, nb);
+            for (int32_t k = 0; k < n; k++) x[k] = fma(h, rhat[k], w[k]);
+            trace_add(fnew, h, th, beta);
+            if (fnew > fx) {
+                /* adaptive restart (function scheme): the new iterate is worse
+                 * than the previous one, so the momentum is dropped */
+                th_prev = 1.0;
+                memcpy(xp, x, nb);
+            } else {
+                th_prev = th;
+            }
+            fx = fnew;
+            h0 = h;
+            it++;
+            if (fnew < fb) { memcpy(xb, x, nb); fb = fnew; xb_is_w_grad = 0; }
+        }
+        memcpy(x, xb, nb);
+        result_f = fb;
+        if (status != ORC_NONFINITE) {
+            if (xb_is_w_grad) {
+                result_ginf = xb_ginf;
+            } else { /* report the gradient of the returned point */
+                result_f = obj_eg(&o, x, g);
+                result_ginf = infnorm(n, g);
+            }
+        }
+        goto done;
+    }
+
+    /* GD, CG, L-BFGS */
+    if (ginf < op->gtol_inf) goto done;
+    for (int32_t k = 0; k < n; k++) r[k] = -g[k];
+    for (;;) {
+        if (CAP_HIT(it, o)) { status = ORC_MAX_ITER; break; }
+        if (method == ORC_LBFGS)
+            orc_lbfgs_direction(n, g, hist, S, Y, op->precond_d, r);
+        else if (method == ORC_GD)
+            for (int32_t k = 0; k < n; k++) r[k] = -g[k];
+        normalise(n, r, rhat);
+        double slope = dotn(n, g, rhat);
+        int32_t ne = 0;
+        double fnew;
+        double h = line_search(op, method, &o, x, rhat, xt, f, slope, h0, &fnew, &ne);
+        if (h == 0.0) {
+            lsf++;
+            if (fresh) { status = ORC_LINESEARCH; break; }
+            fresh = 1;
+            hist = 0;
+            for (int32_t k = 0; k < n; k++) r[k] = -g[k];
+            h0 = op->h0;
+            continue;
+        }
+        fresh = 0;
+        for (int32_t k = 0; k < n; k++) xn[k] = fma(h, rhat[k], x[k]);
+        double fn = obj_eg(&o, xn, gn);
+        if (o.status) { status = o.status; memcpy(x, xn, nb); f = fn; break; }
+        it++;
+        h0 = fabs(h);
+        trace_add(fn, h, 0.0, 0.0);
+        double gninf = infnorm(n, gn);
+        if (method == ORC_LBFGS) {
+            /* s = x+ - x, y = g+ - g; keep the pair only if <s,y> > 0 */
+            double *sn = S + (size_t)(hist < m ? hist : m - 1) * n;
+            double *yn = Y + (size_t)(hist < m ? hist : m - 1) * n;
+            double sy = 0.0;
+            for (int32_t k = 0; k < n; k++) sy += (xn[k] - x[k]) * (gn[k] - g[k]);
+            if (sy > 0.0) {
+                if (hist == m) { /* drop the oldest pair */
+                    memmove(S, S + n, nb * (m - 1));
+                    memmove(Y, Y + n, nb * (m - 1));
+                } else {
+                    hist++;
+                }
+                for (int32_t k = 0; k < n; k++) { sn[k] = xn[k] - x[k]; yn[k] = gn[k] - g[k]; }
+            }
+        } else if (method == ORC_CG) {
+            if (gninf >= op->gtol_inf) {
+                double *rn = xt; /* scratch */
+                if (it % restart_every == 0) {
+                    for (int32_t k = 0; k < n; k++) rn[k] = -gn[k];
+                } else {
+                    double beta = cg_beta(op->cg_variant, n, gn, g, r);
+                    for (int32_t k = 0; k < n; k++) rn[k] = -gn[k] + beta * r[k];
+                    if (dotn(n, gn, rn) >= 0.0)
+                        for (int32_t k = 0; k < n; k++) rn[k] = -gn[k];
+                }
+                memcpy(r, rn, nb);
+            }
+        }
+        memcpy(x, xn, nb);
+        memcpy(g, gn, nb);
+        f = fn;
+        ginf = gninf;
+        if (ginf < op->gtol_inf) { status = ORC_OK; break; }
+    }
+    result_f = f;
+    result_ginf = ginf;
+done:
+    res->energy = result_f;
+    res->grad_inf = result_ginf;
+    res->iterations = it;
+    res->energy_evals = o.ne;
+    res->grad_evals = o.neg;
+    res->ls_failures = lsf;
+    res->status = status;
+    free(g); free(r); free(rhat); free(xt); free(gn); free(xn); free(xp); free(xb);
+    free(S); free(Y);
+    return status;
+}
+
+/* ---------------- force-field objective ---------------- */
+static double ff_fg(void *ctx, const double *x, double *g, int32_t *status) {
+    orc_terms t;
+    *status = orc_energy_terms((const orc_ff *)ctx, x, g, &t);
+    return t.total;
+}
+
+/* gradient-free "parab" (Section 3): move one random atom per step to the
+ * best of 7 axis points (current, +-delta on x, y, z) and the vertex of the
+ * per-axis parabolas; check |grad|_inf once per sweep of N moves. */
+static int parab(const orc_ff *ff, double *x, const orc_options *op, orc_result *res) {
+    const int32_t n = ff->n_atoms;
+    const double dl = op->gradfree_delta;
+    size_t nb = sizeof(double) * 3 * (size_t)n;
+    double *g = malloc(nb);
+    orc_terms t;
+    int status = orc_energy_terms(ff, x, g, &t);
+    int32_t neg = 1, ne = 0, moves = 0;
+    double ginf = infnorm(3 * n, g);
+    trace_reset();
+    if (status == ORC_OK && !(ginf < op->gtol_inf)) {
+        for (;;) {
+            for (int32_t sweep = 0; sweep < n; sweep++) {
+                if (moves >= op->max_iter) { status = ORC_MAX_ITER; break; }
+                int32_t i = orc_pick_atom(op->seed, (uint64_t)moves, n);
+                double p[8][3], fv[8];
+                for (int c = 0; c < 8; c++)
+                    for (int a = 0; a < 3; a++) p[c][a] = x[3 * i + a];
+                for (int a = 0; a < 3; a++) {
+                    p[1 + 2 * a][a] += dl; /* +delta */
+                    p[2 + 2 * a][a] -= dl; /* -delta */
+                }
+                for (int c = 0; c < 7; c++) fv[c] = orc_row_energy(ff, x, i, p[c]);
+                for (int a = 0; a < 3; a++) {
+                    double fp = fv[1 + 2 * a], fm = fv[2 + 2 * a];
+                    double curv = fm - 2.0 * fv[0] + fp;
+                    double ts = curv > 0.0 ? dl * (fm - fp) / (2.0 * curv) : 0.0;
+                    p[7][a] = x[3 * i + a] + ts;
+                }
+                fv[7] = orc_row_energy(ff, x, i, p[7]);
+                ne += 8;
+                int best = 0;
+                for (int c = 1; c < 8; c++)
+                    if (fv[c] < fv[best]) best = c;
+                for (int a = 0; a < 3; a++) x[3 * i + a] = p[best][a];
+                moves++;
+            }
+            if (status == ORC_MAX_ITER) break;
+            status = orc_energy_terms(ff, x, g, &t);
+            neg++;
+            ginf = infnorm(3 * n, g);
+            trace_add(t.total, 0.0, 0.0, 0.0);
+            if (status != ORC_OK) break;
+            if (ginf < op->gtol_inf) break;
+        }
+    }
+    if (status == ORC_MAX_ITER) { /* report the returned point */
+        orc_energy_terms(ff, x, g, &t);
+        neg++;
+        ginf = infnorm(3 * n, g);
+    }
+    res->energy = t.total;
+    res->grad_inf = ginf;
+    res->iterations = moves;
+    res->energy_evals = ne;
+    res->grad_evals = neg;
+    res->ls_failures = 0;
+    res->status = status;
+    free(g);
+    return status;
+}
+
+int orc_minimize_ff(const orc_ff *ff, double *x, const orc_options *o, orc_result *res) {
+    if (o->method == ORC_GRADFREE) return parab(ff, x, o, res);
+    orc_options op = *o;
+    if (op.cg_restart_every <= 0) op.cg_restart_every = 3 * ff->n_atoms;
+    return orc_minimize(3 * ff->n_atoms, ff_fg, (void *)ff, x, &op, res);
+}
