@@ -1,0 +1,334 @@
+"""Benchmark of the force-field minimization hot path on GB300.
+
+Workload (N = 1): the paper-scale 30,000-atom globule (seed 3, the
+10^4-variable scale of the paper is the smaller 3,334-atom case) with the
+plain FP64 pair kernel.  One step = one capped L-BFGS run (m = 10, LS_PAR,
+10 accepted steps = 1 + 10 x 4 evaluations of E or E + grad E) from the
+jittered start: every row of the hot path (pair kernel, bonded terms,
+reductions, line search, two-loop direction, history update, stopping test)
+runs each step.  value = unique pair interactions evaluated per second
+(N(N-1)/2 per evaluation).  The same step in MIXED precision, minimizations
+per second to |grad E|_inf < 0.1 (small batch), the device roofline of the
+dominant kernel and the FP64 CPU oracle are reported beside it.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun every rank runs its own replica (independent systems, no
+collective on the data path); value is the sum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "E+grad pair interactions/s and minimizations/s to ‖∇E‖∞<0.1, vs plain GPU"
+N_ATOMS = 30000
+SEED = 3
+CAP_ITERS = 10
+FLOPS_PER_PAIR_EG = 35.0   # nominal FP32-style count, FMA = 2
+FLOPS_PER_PAIR_E = 23.0
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm = []
+        mx = None
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx = float(r[1])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if r[3 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(p))
+    except Exception:
+        return {}
+
+
+def flush_l2(buf):
+    buf.zero_()
+
+
+def bench_gpu(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    from paper_1810_03358_gb300 import build as gbuild
+    gbuild.build()
+    from paper_1810_03358_gb300 import ffmin, synth
+
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    s = synth.make_system(N_ATOMS, SEED + 1000 * rank)
+    pairs_per_eval = N_ATOMS * (N_ATOMS - 1) // 2
+    x0 = torch.tensor(s.x.reshape(-1), dtype=torch.float64, device=dev)
+    l2 = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def run_steps(S, steps, warmup, e2e=False):
+        x = torch.empty_like(x0)
+        xh = s.x.reshape(-1).copy()
+        pin = torch.empty(x0.numel(), dtype=torch.float64, pin_memory=True)
+        evals = []
+        for _ in range(warmup):
+            x.copy_(x0)
+            S.minimize(x, method="LBFGS", lbfgs_m=10, max_iter=CAP_ITERS)
+        torch.cuda.synchronize()
+        times = []
+        launches = 0
+        for _ in range(steps):
+            flush_l2(l2)
+            x.copy_(x0)
+            barrier()
+            torch.cuda.synchronize()
+            if e2e:
+                t0 = time.perf_counter()
+                pin.copy_(torch.from_numpy(xh))
+                r = S.minimize_host(pin.numpy(), method="LBFGS", lbfgs_m=10, max_iter=CAP_ITERS)
+                torch.cuda.synchronize()
+                times.append(time.perf_counter() - t0)
+            else:
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev1 = torch.cuda.Event(enable_timing=True)
+                ev0.record()
+                r = S.minimize(x, method="LBFGS", lbfgs_m=10, max_iter=CAP_ITERS)
+                ev1.record()
+                torch.cuda.synchronize()
+                times.append(ev0.elapsed_time(ev1) / 1e3)
+            barrier()
+            evals.append(r[0]["energy_evals"] + r[0]["grad_evals"])
+            launches += S.last_stats()["launches"]
+        return times, evals, launches, r[0]
+
+    out = {}
+    sampler = ClockSampler(local if ws > 1 else 0)
+    # ---- primary: plain FP64 ----
+    S64 = ffmin.System([s], ffmin.FFMIN_FP64)
+    sampler.start()
+    t64, ev64, launches, r64 = run_steps(S64, args.steps, args.warmup)
+    clocks = sampler.stop()
+    step_s = max(t64) if False else sum(t64) / len(t64)
+    if ws > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([sum(t64)], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_t = float(tt.item())
+    else:
+        total_t = sum(t64)
+    total_pairs = sum(ev64) * pairs_per_eval * ws
+    value = total_pairs / total_t
+    # e2e through the host entry point (H2D of x and D2H of the result inside)
+    te2e, ev_e2e, _, _ = run_steps(S64, max(1, min(args.steps, 3)), 1, e2e=True)
+    e2e_value = sum(ev_e2e) * pairs_per_eval * ws / sum(te2e)
+    # dominant kernel: FP64 pair kernel, E + grad mode, timed alone on its stream
+    ms_pair = S64.time_pair_kernel(x0, with_grad=True, reps=5)
+    ms_pair_e = S64.time_pair_kernel(x0, with_grad=False, reps=5)
+    S64.close()
+    # ---- mixed precision, same step ----
+    S32 = ffmin.System([s], ffmin.FFMIN_MIXED)
+    t32, ev32, launches32, r32 = run_steps(S32, args.steps, args.warmup)
+    ms_pair32 = S32.time_pair_kernel(x0, with_grad=True, reps=20)
+    S32.close()
+    value32 = sum(ev32) * pairs_per_eval * ws / sum(t32)
+
+    peaks = load_peaks()
+    achieved_fp64 = FLOPS_PER_PAIR_EG * pairs_per_eval / (ms_pair / 1e3) / 1e12
+    achieved_fp32 = FLOPS_PER_PAIR_EG * pairs_per_eval / (ms_pair32 / 1e3) / 1e12
+    sm_clock = clocks.get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median") or 2070.0
+    fp32_peak = 152 * 128 * 2 * 2070e6 / 1e12
+    fp64_peak = float(os.environ.get("FFMIN_FP64_PEAK_TFLOPS", "1.25"))
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "pair interactions/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * total_t / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{N_ATOMS}-atom chain globule (seed {SEED}), plain FP64 path, "
+                               f"L-BFGS m=10 capped at {CAP_ITERS} steps per step",
+                   "n_atoms": N_ATOMS, "evals_per_step": ev64[0], "l2": "flushed (256 MB write) between steps",
+                   "parallelism": f"replicas x{ws}"},
+        "e2e": {"value": e2e_value, "unit": "pair interactions/s",
+                "h2d_bytes_per_step": 8 * 3 * N_ATOMS, "d2h_bytes_per_step": 8 * 3 * N_ATOMS},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "roofline": {"bound": "alu", "achieved": achieved_fp64, "peak": fp64_peak, "unit": "TFLOP/s",
+                     "frac": achieved_fp64 / fp64_peak, "traffic": None,
+                     "kernel": "k_pair<double> (E+grad)", "ms_per_launch": ms_pair,
+                     "flops_per_pair": FLOPS_PER_PAIR_EG, "pairs_per_launch": pairs_per_eval,
+                     "peak_source": "nominal FP64 rate (see DESIGN.md)"},
+        "mixed": {"value": value32, "unit": "pair interactions/s", "ms_per_step": 1e3 * sum(t32) / len(t32),
+                  "vs_plain_gpu": value32 / value, "pair_kernel_ms": ms_pair32,
+                  "achieved_tflops": achieved_fp32, "fp32_peak_tflops_at_max_clock": fp32_peak,
+                  "frac_of_fp32_peak": achieved_fp32 / fp32_peak,
+                  "final_energy": r32["energy"], "final_energy_fp64": r64["energy"]},
+        "pair_kernel_e_only_ms": ms_pair_e,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def cpu_baseline():
+    """The FP64 oracle, as it stands, on one host core: one E + grad E of the
+    same 30,000-atom system (a bounded sample of the step's evaluations)."""
+    from oracle import oracle
+    from paper_1810_03358_gb300 import synth
+    s = synth.make_system(N_ATOMS, SEED)
+    t0 = time.perf_counter()
+    oracle.energy_grad(s, s.x)
+    dt = time.perf_counter() - t0
+    pairs = N_ATOMS * (N_ATOMS - 1) // 2
+    return {"value": pairs / dt, "unit": "pair interactions/s", "cores": 1, "kind": "oracle",
+            "sample": f"one E+grad evaluation of the {N_ATOMS}-atom globule ({dt:.1f} s)"}
+
+
+def bench_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    from oracle import oracle
+    from paper_1810_03358_gb300 import synth
+    s = synth.make_system(N_ATOMS, SEED)
+    pairs = N_ATOMS * (N_ATOMS - 1) // 2
+    for _ in range(args.warmup):
+        oracle.energy(s, s.x[:2000])  # cheap warm-up of the oracle library
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.energy_grad(s, s.x)
+        times.append(time.perf_counter() - t0)
+    value = args.steps * pairs / sum(times)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "pair interactions/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{N_ATOMS}-atom chain globule (seed {SEED}): one E+grad evaluation per step "
+                               "by the FP64 CPU oracle", "n_atoms": N_ATOMS},
+        "cpu_baseline": {"value": value, "unit": "pair interactions/s", "cores": 1, "kind": "oracle",
+                         "sample": "one full E+grad evaluation per step"},
+        "e2e": {"value": value, "unit": "pair interactions/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }))
+
+
+def profile_run(args):
+    """Small fixed workload for ncu captures: one E + grad E of the
+    30,000-atom globule with the MIXED pair kernel, then one with FP64."""
+    import torch
+    from paper_1810_03358_gb300 import build as gbuild
+    gbuild.build()
+    from paper_1810_03358_gb300 import ffmin, synth
+    s = synth.make_system(args.profile_atoms, SEED)
+    x = torch.tensor(s.x.reshape(-1), dtype=torch.float64, device="cuda")
+    for prec in (ffmin.FFMIN_MIXED, ffmin.FFMIN_FP64):
+        S = ffmin.System([s], prec)
+        e, g = S.energy_grad(x)
+        torch.cuda.synchronize()
+        print("profile", prec, e[0])
+        S.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ffmin")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true", help="small fixed workload for ncu")
+    ap.add_argument("--profile-atoms", type=int, default=N_ATOMS)
+    args = ap.parse_args()
+    if args.profile:
+        profile_run(args)
+    elif args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,185 @@
+/*
+ * ffmin — all-pairs force-field energy, gradient and local minimization on
+ * NVIDIA GB300 (sm_103a).  C ABI.
+ *
+ * The operations follow arXiv 1810.03358 ("Algorithms for local minimization
+ * of a force field for 3D macromolecules"):
+ *   - energy: Section 2, E = E_stretch + E_bend + E_torsion + E_cul + E_vdw,
+ *     non-bonded terms over ALL atom pairs (no exclusions), explicit gradient;
+ *   - minimizers: Section 5.1, Algorithms 1 (FGM), 2 (CG), 3-4 (L-BFGS);
+ *     adaptive gradient descent of Section 3 (Eq. 4 with a parabolic step);
+ *     the gradient-free random-atom "parab" moves of Section 3;
+ *   - line searches: Section 5.2, Algorithms 5 (LS_H) and 6 (LS_PAR).
+ *
+ * Conventions
+ *   - Coordinates are FP64, xyz per atom, [3N] contiguous (AoS), in A.
+ *     Energies in kcal/mol, gradients in kcal/mol/A.
+ *   - "_dev" pointers are device pointers the caller owns (e.g. torch
+ *     tensors); "_host" pointers are host memory the caller owns.  The
+ *     library owns all workspace inside the opaque ffmin_system.
+ *   - All GPU work is enqueued on the stream given at ffmin_create; every
+ *     call that returns results to host memory synchronizes that stream.
+ *   - No function aborts or exits.  Errors are returned as ffmin_status; a
+ *     CUDA error is latched in the system, which then refuses further work.
+ *     ffmin_last_error() gives a one-line message.
+ *   - There is no CPU fallback: every computation runs in CUDA kernels.
+ */
+#ifndef FFMIN_H
+#define FFMIN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FFMIN_OK = 0,
+    FFMIN_ERR_INVALID_ARG = 1,
+    FFMIN_ERR_CUDA = 2,
+    FFMIN_ERR_NONFINITE = 3,   /* coincident atoms, or a non-finite E or gradient */
+    FFMIN_ERR_LINESEARCH = 4,  /* no relaxing step, even after one restart (Section 5.1) */
+    FFMIN_ERR_MAX_ITER = 5,    /* iteration or evaluation budget used up */
+    FFMIN_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up */
+    FFMIN_ERR_OOM = 7
+} ffmin_status;
+
+typedef enum { FFMIN_GD = 0, FFMIN_FGM = 1, FFMIN_CG = 2, FFMIN_LBFGS = 3, FFMIN_GRADFREE = 4 } ffmin_method;
+
+/* beta of CG (Section 5.1; Andrei 2008): d = previous unnormalised
+ * direction, y = g+ - g.  PRP g+.y/|g|^2, HS g+.y/d.y, FR |g+|^2/|g|^2,
+ * PRP+ max(0, PRP), CD |g+|^2/(-d.g), LS g+.y/(-d.g), DY |g+|^2/d.y. */
+typedef enum {
+    FFMIN_CG_PRP = 0, FFMIN_CG_HS, FFMIN_CG_FR, FFMIN_CG_PRP_PLUS,
+    FFMIN_CG_CD, FFMIN_CG_LS, FFMIN_CG_DY
+} ffmin_cg_variant;
+
+/* DEFAULT = LS_H for FGM, LS_PAR for GD, CG and L-BFGS. */
+typedef enum { FFMIN_LS_DEFAULT = 0, FFMIN_LS_H = 1, FFMIN_LS_PAR = 2 } ffmin_linesearch;
+
+/* FP64: every pair term in FP64.  MIXED: pair terms in FP32 with FP32
+ * accumulation inside a j-chunk; per-atom sums, energy totals, the line
+ * search, every dot product and all vector updates stay FP64. */
+typedef enum { FFMIN_FP64 = 0, FFMIN_MIXED = 1 } ffmin_precision;
+
+/* One system (host arrays, FP64 / int32, copied at ffmin_create; the
+ * caller keeps ownership).  Atom indices are 0-based within the system. */
+typedef struct {
+    int32_t n_atoms;
+    const double *charge, *sigma, *epsilon;            /* [N] e, A, kcal/mol */
+    int32_t n_bonds;
+    const int32_t *bond_idx;                           /* [nb*2] */
+    const double *bond_k, *bond_r0;                    /* [nb] E = K (r - r0)^2 */
+    int32_t n_angles;
+    const int32_t *angle_idx;                          /* [na*3], vertex in the middle */
+    const double *angle_k, *angle_theta0;              /* [na] E = K (theta - theta0)^2, rad */
+    int32_t n_dihedrals;
+    const int32_t *dihedral_idx;                       /* [nd*4] */
+    const double *dihedral_v;                          /* [nd*4] V1..V4 */
+    double coulomb_c;  /* 0 -> 332.0716 kcal*A/(mol*e^2) = 1389.38757 / 4.184 (Section 2) */
+} ffmin_topology;
+
+typedef struct {
+    int32_t method;          /* ffmin_method, default FFMIN_LBFGS */
+    int32_t cg_variant;      /* ffmin_cg_variant, default PRP */
+    int32_t ls;              /* ffmin_linesearch, default DEFAULT */
+    int32_t lbfgs_m;         /* history pairs, 1..16, default 10 */
+    double gtol_inf;         /* stop when max_k |dE/dx_k| < gtol_inf; default 0.1 kcal/mol/A */
+    int32_t max_iter;        /* accepted steps (GRADFREE: atom moves), default 100000 */
+    int32_t max_evals;       /* energy + gradient evaluations, default 1000000 */
+    int32_t cg_restart_every;/* 0 -> 3N */
+    double h0;               /* first trial step (A), default 0.1 */
+    double k_plus, k_minus;  /* step growth / shrink factors, default 2 and 0.5 */
+    double eps_h;            /* LS_H smallest step, default 1e-10 */
+    int32_t ls_par_K;        /* LS_PAR refinement bound K >= 2, default 2 */
+    int32_t ls_par_g0;       /* LS_PAR uses the slope at 0 (G0), default 1 */
+    double gradfree_delta;   /* GRADFREE axis offset (A), default 0.05 */
+    uint64_t seed;           /* GRADFREE atom picker seed (SplitMix64 stream) */
+    int32_t use_learned_precond; /* L-BFGS: scale H0 by the learned per-atom diagonal */
+    int32_t max_ticks;       /* safety bound on device evaluation rounds; 0 -> max_evals + 64 */
+} ffmin_options;
+
+typedef struct {
+    double energy;           /* E at the returned point */
+    double grad_inf;         /* max_k |dE/dx_k| at the returned point */
+    int32_t iterations;      /* accepted steps (GRADFREE: moves) */
+    int32_t energy_evals;    /* energy-only evaluations (GRADFREE: row evaluations) */
+    int32_t grad_evals;      /* energy + gradient evaluations */
+    int32_t ls_failures;
+    int32_t stop_reason;     /* ffmin_status: OK when converged */
+} ffmin_result;
+
+typedef struct ffmin_system ffmin_system;
+
+/* Fill *o with the defaults above. */
+void ffmin_options_default(ffmin_options *o);
+
+/* Human-readable name of a status. */
+const char *ffmin_status_string(ffmin_status s);
+
+/* Create a batch of n_sys >= 1 systems (their atoms are concatenated in
+ * the order given: system b owns atoms [A_b, A_b + N_b) of every
+ * coordinate / gradient buffer).  precision: ffmin_precision.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ * Errors: INVALID_ARG (bad counts or indices), OOM, CUDA. */
+ffmin_status ffmin_create(const ffmin_topology *systems, int32_t n_sys, int32_t precision,
+                          void *cuda_stream, ffmin_system **out);
+
+/* Free every device and host resource of the system. */
+ffmin_status ffmin_destroy(ffmin_system *sys);
+
+/* Total atom count over the batch; per-system atom offset of system b. */
+int64_t ffmin_n_atoms(const ffmin_system *sys);
+int64_t ffmin_atom_offset(const ffmin_system *sys, int32_t b);
+
+/* Energy of every system at x_dev [3 * total atoms] (device, FP64):
+ * e_host[n_sys].  Section 2.  Synchronizes the stream. */
+ffmin_status ffmin_energy(ffmin_system *sys, const double *x_dev, double *e_host);
+
+/* Energy and gradient: e_host[n_sys], g_dev [3 * total atoms] (device). */
+ffmin_status ffmin_energy_grad(ffmin_system *sys, const double *x_dev, double *e_host,
+                               double *g_dev);
+
+/* Same with host buffers: copies x_host to the device, evaluates, and
+ * copies the gradient back to g_host (pass NULL to skip it). */
+ffmin_status ffmin_energy_grad_host(ffmin_system *sys, const double *x_host, double *e_host,
+                                    double *g_host);
+
+/* Minimize every system of the batch from x_dev (device, in/out): on
+ * return x_dev holds each system's result and results[n_sys] its record.
+ * The call's status is FFMIN_OK when it ran; each system's own outcome is
+ * in results[b].stop_reason.  method GRADFREE requires n_sys == 1. */
+ffmin_status ffmin_minimize(ffmin_system *sys, double *x_dev, const ffmin_options *opt,
+                            ffmin_result *results);
+
+/* Same with a host coordinate buffer (copied in and out). */
+ffmin_status ffmin_minimize_host(ffmin_system *sys, double *x_host, const ffmin_options *opt,
+                                 ffmin_result *results);
+
+/* Learned L-BFGS preconditioner: a per-atom MLP 5 -> 64 -> 1 (ReLU hidden
+ * layer) with FP16 weights, applied when options.use_learned_precond is set.
+ * w_fp16 holds 449 half-precision values: W1 [64][5], b1 [64], W2 [64], b2.
+ * Features per atom: q, sigma, epsilon, n(8 A)/64, log(1 + |g_i|).
+ * H0 = gamma * diag(exp(clamp(z_i, -3, 3))) over the atom's 3 coordinates.
+ * The paper has no counterpart; this is an extension of Algorithm 3. */
+ffmin_status ffmin_set_precond(ffmin_system *sys, const uint16_t *w_fp16_host, int32_t n_params);
+
+/* Time the dominant pair kernel alone: reps launches at x_dev with (1) or
+ * without (0) forces, CUDA events on the system's stream; *ms = mean
+ * duration of one launch.  Diagnostic for roofline reporting. */
+ffmin_status ffmin_time_pair_kernel(ffmin_system *sys, const double *x_dev, int32_t with_grad,
+                                    int32_t reps, float *ms);
+
+/* Work done by the last ffmin_minimize: pair kernel launches and device
+ * evaluation rounds; n_kernel_launches counts every kernel launched. */
+ffmin_status ffmin_last_stats(const ffmin_system *sys, int64_t *ticks,
+                              int64_t *n_kernel_launches, int64_t *pair_interactions);
+
+/* Last error message of the system (or of the last failed create). */
+const char *ffmin_last_error(const ffmin_system *sys);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -58,6 +58,10 @@ int orc_energy_terms(const orc_ff *ff, const double *x, double *grad, orc_terms 
  * moves (pair terms with i plus bonded terms containing i). */
 double orc_row_energy(const orc_ff *ff, const double *x, int32_t i, const double p[3]);
 
+/* Gradient of E with respect to atom i alone (g3[3]); pair row plus the
+ * bonded terms that contain atom i. */
+int orc_atom_gradient(const orc_ff *ff, const double *x, int32_t i, double *g3);
+
 /* Neighbour count of atom i: atoms j != i with |x_i - x_j| < rc. */
 int32_t orc_neighbour_count(const orc_ff *ff, const double *x, int32_t i, double rc);
 

@@ -267,3 +267,46 @@ int32_t orc_neighbour_count(const orc_ff *ff, const double *x, int32_t i, double
     }
     return c;
 }
+
+/* Gradient of E with respect to the position of atom i only (g3[3]): the
+ * pair terms of row i plus every bonded term containing i. */
+int orc_atom_gradient(const orc_ff *ff, const double *x, int32_t i, double *g3) {
+    int status = ORC_OK;
+    g3[0] = g3[1] = g3[2] = 0.0;
+    for (int j = 0; j < ff->n_atoms; j++) {
+        if (j == i) continue;
+        double d[3], ec, ev, f;
+        sub3(x + 3 * i, x + 3 * j, d);
+        if (dot3(d, d) == 0.0) { status = ORC_NONFINITE; continue; }
+        pair_term(ff->coulomb_c, ff->charge[i], ff->charge[j], ff->sigma[i], ff->sigma[j],
+                  ff->epsilon[i], ff->epsilon[j], d, &ec, &ev, &f);
+        for (int a = 0; a < 3; a++) g3[a] += f * d[a];
+    }
+    for (int b = 0; b < ff->n_bonds; b++) {
+        const int32_t *q = ff->bond_idx + 2 * b;
+        if (q[0] != i && q[1] != i) continue;
+        double g[2][3];
+        bond_term(x + 3 * q[0], x + 3 * q[1], ff->bond_k[b], ff->bond_r0[b], g[0], g[1]);
+        for (int p = 0; p < 2; p++)
+            if (q[p] == i) for (int a = 0; a < 3; a++) g3[a] += g[p][a];
+    }
+    for (int b = 0; b < ff->n_angles; b++) {
+        const int32_t *q = ff->angle_idx + 3 * b;
+        if (q[0] != i && q[1] != i && q[2] != i) continue;
+        double g[3][3];
+        angle_term(x + 3 * q[0], x + 3 * q[1], x + 3 * q[2], ff->angle_k[b], ff->angle_theta0[b],
+                   g[0], g[1], g[2]);
+        for (int p = 0; p < 3; p++)
+            if (q[p] == i) for (int a = 0; a < 3; a++) g3[a] += g[p][a];
+    }
+    for (int b = 0; b < ff->n_dihedrals; b++) {
+        const int32_t *q = ff->dihedral_idx + 4 * b;
+        if (q[0] != i && q[1] != i && q[2] != i && q[3] != i) continue;
+        double g[4][3];
+        dihedral_term(x + 3 * q[0], x + 3 * q[1], x + 3 * q[2], x + 3 * q[3],
+                      ff->dihedral_v + 4 * b, g[0], g[1], g[2], g[3], NULL);
+        for (int p = 0; p < 4; p++)
+            if (q[p] == i) for (int a = 0; a < 3; a++) g3[a] += g[p][a];
+    }
+    return status;
+}

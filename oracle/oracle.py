@@ -67,6 +67,8 @@ def lib():
         L.orc_energy_terms.restype = C.c_int
         L.orc_row_energy.argtypes = [C.POINTER(_FF), _dp, C.c_int32, _dp]
         L.orc_row_energy.restype = C.c_double
+        L.orc_atom_gradient.argtypes = [C.POINTER(_FF), _dp, C.c_int32, _dp]
+        L.orc_atom_gradient.restype = C.c_int
         L.orc_neighbour_count.argtypes = [C.POINTER(_FF), _dp, C.c_int32, C.c_double]
         L.orc_neighbour_count.restype = C.c_int32
         L.orc_ls_h.argtypes = [LINE_FN, C.c_void_p, C.c_double, C.c_double, C.c_double,
@@ -153,6 +155,15 @@ def row_energy(s, x, i, p):
     xx = _f64(x).reshape(-1)
     pp = _f64(p).reshape(3)
     return lib().orc_row_energy(C.byref(f.s), _dptr(xx), int(i), _dptr(pp))
+
+
+def atom_gradient(s, x, i):
+    """dE/dx_i of one atom (3,), computed from its own terms only."""
+    f = _ff(s)
+    xx = _f64(x).reshape(-1)
+    g = np.zeros(3)
+    lib().orc_atom_gradient(C.byref(f.s), _dptr(xx), int(i), _dptr(g))
+    return g
 
 
 def neighbour_count(s, x, i, rc=8.0):

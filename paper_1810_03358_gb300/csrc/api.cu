@@ -1,0 +1,710 @@
+// C ABI of the ffmin library (declared in include/ffmin.h): creation of a
+// batch of systems, energy / gradient evaluation and the minimization driver.
+//
+// The driver keeps every decision on the device: it replays a CUDA graph of
+// TICKS pipeline rounds (update, two direction passes, prepare, pair,
+// finalize) on the library's own stream and reads back one counter of
+// still-active systems per replay.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ffmin_internal.cuh"
+
+using namespace ffm;
+
+namespace ffm {
+cudaError_t parab_minimize(ffmin_system *sys, const ffmin_options *o, ffmin_result *res);
+}
+
+struct ffmin_system {
+    int n_sys = 0;
+    int64_t n_atoms = 0;
+    int prec = 0;
+    cudaStream_t user_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    bool broken = false;
+    std::string err;
+    Ctx c{};
+    std::vector<void *> allocs;
+    std::vector<int64_t> atom_off;
+    std::vector<int32_t> sys_natoms;
+    std::vector<SysState> hst;
+    int pair_grid = 0;
+    int graph_ticks = 0;
+    cudaGraphExec_t graph = nullptr;
+    int32_t *h_nactive = nullptr;  // pinned
+    // learned preconditioner
+    bool have_precond = false;
+    // stats of the last minimize
+    int64_t last_ticks = 0, last_launches = 0, last_pairs = 0;
+    // host copies of the topology needed by the gradient-free path
+    std::vector<int32_t> inc_off_h;
+};
+
+static thread_local std::string g_create_err;
+
+static ffmin_status fail(ffmin_system *s, ffmin_status st, const std::string &msg) {
+    if (s) s->err = msg;
+    else g_create_err = msg;
+    return st;
+}
+
+static ffmin_status cuda_fail(ffmin_system *s, cudaError_t e, const char *where) {
+    if (s) {
+        s->broken = true;
+        s->err = std::string(where) + ": " + cudaGetErrorString(e);
+    } else {
+        g_create_err = std::string(where) + ": " + cudaGetErrorString(e);
+    }
+    return e == cudaErrorMemoryAllocation ? FFMIN_ERR_OOM : FFMIN_ERR_CUDA;
+}
+
+#define CK(call)                                                     \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return cuda_fail(sys, e_, #call);     \
+    } while (0)
+
+template <typename T>
+static cudaError_t dalloc(ffmin_system *sys, T **p, size_t count) {
+    size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc((void **)p, bytes);
+    if (e != cudaSuccess) return e;
+    sys->allocs.push_back(*p);
+    return cudaMemsetAsync(*p, 0, bytes, sys->stream);
+}
+
+template <typename T>
+static cudaError_t upload(ffmin_system *sys, T **p, const std::vector<T> &h) {
+    cudaError_t e = dalloc(sys, p, h.size());
+    if (e != cudaSuccess || h.empty()) return e;
+    return cudaMemcpyAsync(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, sys->stream);
+}
+
+extern "C" {
+
+void ffmin_options_default(ffmin_options *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->method = FFMIN_LBFGS;
+    o->cg_variant = FFMIN_CG_PRP;
+    o->ls = FFMIN_LS_DEFAULT;
+    o->lbfgs_m = 10;
+    o->gtol_inf = 0.1;
+    o->max_iter = 100000;
+    o->max_evals = 1000000;
+    o->cg_restart_every = 0;
+    o->h0 = 0.1;
+    o->k_plus = 2.0;
+    o->k_minus = 0.5;
+    o->eps_h = 1e-10;
+    o->ls_par_K = 2;
+    o->ls_par_g0 = 1;
+    o->gradfree_delta = 0.05;
+    o->seed = 12345;
+    o->use_learned_precond = 0;
+    o->max_ticks = 0;
+}
+
+const char *ffmin_status_string(ffmin_status s) {
+    switch (s) {
+    case FFMIN_OK: return "ok";
+    case FFMIN_ERR_INVALID_ARG: return "invalid argument";
+    case FFMIN_ERR_CUDA: return "cuda error";
+    case FFMIN_ERR_NONFINITE: return "non-finite energy or gradient";
+    case FFMIN_ERR_LINESEARCH: return "line search failed";
+    case FFMIN_ERR_MAX_ITER: return "iteration limit";
+    case FFMIN_ERR_TIMEOUT: return "device round limit";
+    case FFMIN_ERR_OOM: return "out of memory";
+    }
+    return "unknown";
+}
+
+const char *ffmin_last_error(const ffmin_system *sys) {
+    return sys ? sys->err.c_str() : g_create_err.c_str();
+}
+
+int64_t ffmin_n_atoms(const ffmin_system *sys) { return sys ? sys->n_atoms : 0; }
+
+int64_t ffmin_atom_offset(const ffmin_system *sys, int32_t b) {
+    if (!sys || b < 0 || b > sys->n_sys) return -1;
+    return sys->atom_off[b];
+}
+
+ffmin_status ffmin_destroy(ffmin_system *sys) {
+    if (!sys) return FFMIN_ERR_INVALID_ARG;
+    if (sys->stream) cudaStreamSynchronize(sys->stream);
+    if (sys->graph) cudaGraphExecDestroy(sys->graph);
+    for (void *p : sys->allocs) cudaFree(p);
+    if (sys->h_nactive) cudaFreeHost(sys->h_nactive);
+    if (sys->ev_in) cudaEventDestroy(sys->ev_in);
+    if (sys->ev_out) cudaEventDestroy(sys->ev_out);
+    if (sys->stream) cudaStreamDestroy(sys->stream);
+    delete sys;
+    return FFMIN_OK;
+}
+
+static bool idx_ok(const int32_t *idx, int64_t count, int32_t n) {
+    for (int64_t k = 0; k < count; k++)
+        if (idx[k] < 0 || idx[k] >= n) return false;
+    return true;
+}
+
+// j-chunk length of a system: a multiple of TJ, chosen so that the whole
+// batch exposes at least ~4 work items per resident pair-kernel block
+static int chunk_len(int32_t n, int64_t total_tiles, int grid) {
+    int64_t want_items = 4LL * grid;
+    int64_t chunks = std::max<int64_t>(1, (want_items + total_tiles - 1) / std::max<int64_t>(total_tiles, 1));
+    int64_t len = (n + chunks - 1) / chunks;
+    len = ((len + TJ - 1) / TJ) * TJ;
+    len = std::max<int64_t>(len, TJ);
+    return (int)len;
+}
+
+ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t precision,
+                          void *cuda_stream, ffmin_system **out) {
+    if (!out) return fail(nullptr, FFMIN_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!tops || n_sys < 1) return fail(nullptr, FFMIN_ERR_INVALID_ARG, "need n_sys >= 1 topologies");
+    if (precision != FFMIN_FP64 && precision != FFMIN_MIXED)
+        return fail(nullptr, FFMIN_ERR_INVALID_ARG, "precision must be FFMIN_FP64 or FFMIN_MIXED");
+    int64_t total = 0;
+    for (int b = 0; b < n_sys; b++) {
+        const ffmin_topology &t = tops[b];
+        if (t.n_atoms < 1 || t.n_bonds < 0 || t.n_angles < 0 || t.n_dihedrals < 0)
+            return fail(nullptr, FFMIN_ERR_INVALID_ARG, "negative or zero count in topology " + std::to_string(b));
+        if (!t.charge || !t.sigma || !t.epsilon)
+            return fail(nullptr, FFMIN_ERR_INVALID_ARG, "missing per-atom arrays in topology " + std::to_string(b));
+        if ((t.n_bonds && (!t.bond_idx || !t.bond_k || !t.bond_r0)) ||
+            (t.n_angles && (!t.angle_idx || !t.angle_k || !t.angle_theta0)) ||
+            (t.n_dihedrals && (!t.dihedral_idx || !t.dihedral_v)))
+            return fail(nullptr, FFMIN_ERR_INVALID_ARG, "missing bonded arrays in topology " + std::to_string(b));
+        if (!idx_ok(t.bond_idx, 2LL * t.n_bonds, t.n_atoms) || !idx_ok(t.angle_idx, 3LL * t.n_angles, t.n_atoms) ||
+            !idx_ok(t.dihedral_idx, 4LL * t.n_dihedrals, t.n_atoms))
+            return fail(nullptr, FFMIN_ERR_INVALID_ARG, "atom index out of range in topology " + std::to_string(b));
+        for (int a = 0; a < t.n_atoms; a++)
+            if (!(t.sigma[a] >= 0.0) || !(t.epsilon[a] >= 0.0) || !std::isfinite(t.charge[a]))
+                return fail(nullptr, FFMIN_ERR_INVALID_ARG, "sigma/epsilon must be >= 0 and charges finite");
+        total += t.n_atoms;
+    }
+    if (total > (1LL << 30)) return fail(nullptr, FFMIN_ERR_INVALID_ARG, "too many atoms");
+
+    ffmin_system *sys = new ffmin_system();
+    sys->n_sys = n_sys;
+    sys->n_atoms = total;
+    sys->prec = precision;
+    sys->user_stream = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaStreamCreateWithFlags(&sys->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { ffmin_status st = cuda_fail(nullptr, e, "cudaStreamCreate"); delete sys; return st; }
+    cudaEventCreateWithFlags(&sys->ev_in, cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&sys->ev_out, cudaEventDisableTiming);
+    if (cudaMallocHost((void **)&sys->h_nactive, sizeof(int32_t)) != cudaSuccess) {
+        ffmin_destroy(sys);
+        return fail(nullptr, FFMIN_ERR_OOM, "pinned allocation failed");
+    }
+    sys->pair_grid = pair_grid_size(precision);
+
+    // ---- tiles, items, per-atom data, bonded terms ----
+    std::vector<Tile> tiles;
+    std::vector<Item> items;
+    std::vector<int32_t> tile0(n_sys), ntile(n_sys);
+    sys->atom_off.assign(n_sys + 1, 0);
+    for (int b = 0; b < n_sys; b++) sys->atom_off[b + 1] = sys->atom_off[b] + tops[b].n_atoms;
+    int64_t total_tiles = 0;
+    for (int b = 0; b < n_sys; b++) total_tiles += (tops[b].n_atoms + TI - 1) / TI;
+    std::vector<double> qs(total), sig(total), aa(total);
+    std::vector<float2> parf(total);
+    std::vector<double2> pard(total);
+    std::vector<float> feat(3 * total);
+    std::vector<int2> bidx, aidx_dummy;
+    std::vector<double2> bpar, apar;
+    std::vector<int4> aidx, didx;
+    std::vector<double4_32a> dpar;
+    std::vector<std::vector<int2>> inc_lists(total);
+    for (int b = 0; b < n_sys; b++) {
+        const ffmin_topology &t = tops[b];
+        const int64_t A = sys->atom_off[b];
+        const double C = t.coulomb_c > 0.0 ? t.coulomb_c : 1389.38757 / 4.184;
+        const double sc = std::sqrt(C);
+        for (int a = 0; a < t.n_atoms; a++) {
+            qs[A + a] = t.charge[a] * sc;
+            sig[A + a] = t.sigma[a];
+            aa[A + a] = std::sqrt(24.0 * t.epsilon[a]);
+            const double s3 = sig[A + a] * sig[A + a] * sig[A + a];
+            const double c6 = aa[A + a] * s3, c12 = aa[A + a] * s3 * s3;
+            parf[A + a] = make_float2((float)c6, (float)c12);
+            pard[A + a] = make_double2(c6, c12);
+            feat[3 * (A + a)] = (float)t.charge[a];
+            feat[3 * (A + a) + 1] = (float)t.sigma[a];
+            feat[3 * (A + a) + 2] = (float)t.epsilon[a];
+        }
+        for (int k = 0; k < t.n_bonds; k++) {
+            int term = (int)bidx.size();
+            int i = t.bond_idx[2 * k], j = t.bond_idx[2 * k + 1];
+            bidx.push_back(make_int2((int)(A + i), (int)(A + j)));
+            bpar.push_back(make_double2(t.bond_k[k], t.bond_r0[k]));
+            inc_lists[A + i].push_back(make_int2((0 << 2) | 0, term));
+            inc_lists[A + j].push_back(make_int2((0 << 2) | 1, term));
+        }
+        for (int k = 0; k < t.n_angles; k++) {
+            int term = (int)aidx.size();
+            const int32_t *q = t.angle_idx + 3 * k;
+            aidx.push_back(make_int4((int)(A + q[0]), (int)(A + q[1]), (int)(A + q[2]), 0));
+            apar.push_back(make_double2(t.angle_k[k], t.angle_theta0[k]));
+            for (int p = 0; p < 3; p++) inc_lists[A + q[p]].push_back(make_int2((1 << 2) | p, term));
+        }
+        for (int k = 0; k < t.n_dihedrals; k++) {
+            int term = (int)didx.size();
+            const int32_t *q = t.dihedral_idx + 4 * k;
+            didx.push_back(make_int4((int)(A + q[0]), (int)(A + q[1]), (int)(A + q[2]), (int)(A + q[3])));
+            const double *v = t.dihedral_v + 4 * k;
+            dpar.push_back(make_double4_32a(v[0], v[1], v[2], v[3]));
+            for (int p = 0; p < 4; p++) inc_lists[A + q[p]].push_back(make_int2((2 << 2) | p, term));
+        }
+        // tiles and (tile, j-chunk) items
+        tile0[b] = (int)tiles.size();
+        const int L = chunk_len(t.n_atoms, total_tiles, sys->pair_grid);
+        for (int a0 = 0; a0 < t.n_atoms; a0 += TI) {
+            Tile tl{};
+            tl.sys = b;
+            tl.a0 = (int)(A + a0);
+            tl.na = std::min(TI, t.n_atoms - a0);
+            tl.item0 = (int)items.size();
+            int cnt = 0;
+            for (int j0 = 0; j0 < t.n_atoms; j0 += L) {
+                Item it{};
+                it.tile = (int)tiles.size();
+                it.j0 = (int)(A + j0);
+                it.nj = std::min(L, t.n_atoms - j0);
+                it.diag = (a0 >= j0 && a0 < j0 + it.nj) ? 1 : 0;
+                items.push_back(it);
+                cnt++;
+            }
+            tl.nitem = cnt;
+            tiles.push_back(tl);
+        }
+        ntile[b] = (int)tiles.size() - tile0[b];
+    }
+    std::vector<int32_t> inc_off(total + 1, 0);
+    std::vector<int2> inc;
+    for (int64_t a = 0; a < total; a++) {
+        inc_off[a] = (int32_t)inc.size();
+        for (const int2 &x : inc_lists[a]) inc.push_back(x);
+    }
+    inc_off[total] = (int32_t)inc.size();
+    sys->inc_off_h = inc_off;
+
+    Ctx &c = sys->c;
+    c.n_sys = n_sys;
+    c.n_tiles = (int)tiles.size();
+    c.n_items = (int)items.size();
+    c.n_atoms = (int)total;
+    c.vstride = ((3 * total + 31) / 32) * 32;
+    c.prec = precision;
+
+#define CKC(call)                                                              \
+    do {                                                                       \
+        cudaError_t e_ = (call);                                               \
+        if (e_ != cudaSuccess) {                                               \
+            ffmin_status st_ = cuda_fail(nullptr, e_, #call);                  \
+            ffmin_destroy(sys);                                                \
+            return st_;                                                        \
+        }                                                                      \
+    } while (0)
+
+    Tile *d_tiles; Item *d_items;
+    CKC(upload(sys, &d_tiles, tiles));
+    CKC(upload(sys, &d_items, items));
+    c.tiles = d_tiles;
+    c.items = d_items;
+    SysState *d_st;
+    CKC(dalloc(sys, &d_st, n_sys));
+    c.st = d_st;
+    CKC(dalloc(sys, &c.vec, (size_t)V_NSLOT * c.vstride));
+    double *d_qs;
+    CKC(upload(sys, &d_qs, qs));
+    c.qs = d_qs;
+    if (precision == FFMIN_MIXED) {
+        float2 *d_parf;
+        CKC(dalloc(sys, &c.posf, total));
+        CKC(upload(sys, &d_parf, parf));
+        c.parf = d_parf;
+        CKC(dalloc(sys, &c.gpf, (size_t)c.n_items * TI));
+    } else {
+        double2 *d_pard;
+        CKC(dalloc(sys, &c.posd, total));
+        CKC(upload(sys, &d_pard, pard));
+        c.pard = d_pard;
+        CKC(dalloc(sys, &c.gpd, (size_t)c.n_items * TI));
+    }
+    int32_t *d_inc_off; int2 *d_inc, *d_bidx; double2 *d_bpar, *d_apar; int4 *d_aidx, *d_didx; double4_32a *d_dpar;
+    CKC(upload(sys, &d_inc_off, inc_off));
+    CKC(upload(sys, &d_inc, inc));
+    CKC(upload(sys, &d_bidx, bidx));
+    CKC(upload(sys, &d_bpar, bpar));
+    CKC(upload(sys, &d_aidx, aidx));
+    CKC(upload(sys, &d_apar, apar));
+    CKC(upload(sys, &d_didx, didx));
+    CKC(upload(sys, &d_dpar, dpar));
+    c.inc_off = d_inc_off; c.inc = d_inc; c.bidx = d_bidx; c.bpar = d_bpar;
+    c.aidx = d_aidx; c.apar = d_apar; c.didx = d_didx; c.dpar = d_dpar;
+    CKC(dalloc(sys, &c.red, (size_t)c.n_tiles * NRED));
+    CKC(dalloc(sys, &c.counters, CNT_N));
+    CKC(dalloc(sys, &c.nactive, 1));
+    float *d_feat;
+    CKC(upload(sys, &d_feat, feat));
+    c.feat = d_feat;
+    CKC(dalloc(sys, &c.ncount, total));
+    uint16_t *d_w;
+    CKC(dalloc(sys, &d_w, 512));
+    c.mlp_w = d_w;
+
+    // host mirror of the per-system state (geometry part)
+    sys->hst.assign(n_sys, SysState{});
+    sys->sys_natoms.resize(n_sys);
+    for (int b = 0; b < n_sys; b++) {
+        SysState &S = sys->hst[b];
+        std::memset(&S, 0, sizeof(S));
+        S.atom0 = (int)sys->atom_off[b];
+        S.natoms = tops[b].n_atoms;
+        S.tile0 = tile0[b];
+        S.ntile = ntile[b];
+        sys->sys_natoms[b] = tops[b].n_atoms;
+    }
+    CKC(cudaMemcpyAsync(d_st, sys->hst.data(), sizeof(SysState) * n_sys, cudaMemcpyHostToDevice, sys->stream));
+    CKC(cudaStreamSynchronize(sys->stream));
+#undef CKC
+    *out = sys;
+    return FFMIN_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- helpers
+static ffmin_status enter(ffmin_system *sys) {
+    if (!sys) return FFMIN_ERR_INVALID_ARG;
+    if (sys->broken) return FFMIN_ERR_CUDA;
+    cudaError_t e = cudaEventRecord(sys->ev_in, sys->user_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sys->stream, sys->ev_in, 0);
+    if (e != cudaSuccess) return cuda_fail(sys, e, "stream ordering");
+    return FFMIN_OK;
+}
+
+static ffmin_status leave(ffmin_system *sys) {
+    cudaError_t e = cudaEventRecord(sys->ev_out, sys->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sys->user_stream, sys->ev_out, 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(sys->stream);
+    if (e != cudaSuccess) return cuda_fail(sys, e, "stream sync");
+    return FFMIN_OK;
+}
+
+static ffmin_status upload_states(ffmin_system *sys) {
+    CK(cudaMemcpyAsync(sys->c.st, sys->hst.data(), sizeof(SysState) * sys->n_sys, cudaMemcpyHostToDevice,
+                       sys->stream));
+    return FFMIN_OK;
+}
+
+static ffmin_status download_states(ffmin_system *sys) {
+    CK(cudaMemcpyAsync(sys->hst.data(), sys->c.st, sizeof(SysState) * sys->n_sys, cudaMemcpyDeviceToHost,
+                       sys->stream));
+    CK(cudaStreamSynchronize(sys->stream));
+    return FFMIN_OK;
+}
+
+static cudaError_t launch_tick(ffmin_system *sys) {
+    const Ctx &c = sys->c;
+    cudaError_t e;
+    if ((e = launch_update(c, sys->stream)) != cudaSuccess) return e;
+    if ((e = launch_dir(c, 0, sys->stream)) != cudaSuccess) return e;
+    if ((e = launch_dir(c, 1, sys->stream)) != cudaSuccess) return e;
+    if ((e = launch_prepare(c, sys->stream)) != cudaSuccess) return e;
+    if ((e = launch_pair(c, sys->pair_grid, sys->stream)) != cudaSuccess) return e;
+    return launch_finalize(c, sys->stream);
+}
+
+static const int TICKS_PER_GRAPH = 8;
+static const int KERNELS_PER_TICK = 6;
+
+static ffmin_status ensure_graph(ffmin_system *sys) {
+    if (sys->graph) return FFMIN_OK;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(sys->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int t = 0; t < TICKS_PER_GRAPH && e == cudaSuccess; t++) e = launch_tick(sys);
+    cudaError_t e2 = cudaStreamEndCapture(sys->stream, &g);
+    if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(sys, e, "graph capture"); }
+    if (e2 != cudaSuccess) return cuda_fail(sys, e2, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&sys->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(sys, e, "cudaGraphInstantiate");
+    sys->graph_ticks = TICKS_PER_GRAPH;
+    return FFMIN_OK;
+}
+
+// one evaluation (E or EG) of every system at x (device)
+static ffmin_status eval_all(ffmin_system *sys, const double *x_dev, int kind) {
+    const Ctx &c = sys->c;
+    CK(cudaMemcpyAsync(vslot(c, V_XIN), x_dev, sizeof(double) * 3 * sys->n_atoms, cudaMemcpyDeviceToDevice,
+                       sys->stream));
+    for (int b = 0; b < sys->n_sys; b++) {
+        SysState &S = sys->hst[b];
+        S.active = 1;
+        S.phase = PH_EVAL_ONLY;
+        S.upd.op = U_NONE;
+        S.dir[0].on = S.dir[1].on = 0;
+        S.ev_kind = kind;
+        S.ev_base = V_XIN;
+        S.ev_dir = -1;
+        S.ev_h = 0.0;
+        S.ev_scale = 1.0;
+        S.ne = S.neg = 0;
+    }
+    ffmin_status st = upload_states(sys);
+    if (st != FFMIN_OK) return st;
+    int32_t n = sys->n_sys;
+    CK(cudaMemcpyAsync(c.nactive, &n, sizeof(int32_t), cudaMemcpyHostToDevice, sys->stream));
+    CK(launch_prepare(c, sys->stream));
+    CK(launch_pair(c, sys->pair_grid, sys->stream));
+    CK(launch_finalize(c, sys->stream));
+    return download_states(sys);
+}
+
+extern "C" {
+
+ffmin_status ffmin_energy(ffmin_system *sys, const double *x_dev, double *e_host) {
+    ffmin_status st = enter(sys);
+    if (st != FFMIN_OK) return st;
+    if (!x_dev || !e_host) return fail(sys, FFMIN_ERR_INVALID_ARG, "NULL argument");
+    st = eval_all(sys, x_dev, EV_E);
+    if (st != FFMIN_OK) return st;
+    ffmin_status res = FFMIN_OK;
+    for (int b = 0; b < sys->n_sys; b++) {
+        e_host[b] = sys->hst[b].res_f;
+        if (sys->hst[b].status == FFMIN_ERR_NONFINITE) res = FFMIN_ERR_NONFINITE;
+    }
+    st = leave(sys);
+    return st != FFMIN_OK ? st : res;
+}
+
+ffmin_status ffmin_energy_grad(ffmin_system *sys, const double *x_dev, double *e_host, double *g_dev) {
+    ffmin_status st = enter(sys);
+    if (st != FFMIN_OK) return st;
+    if (!x_dev || !e_host || !g_dev) return fail(sys, FFMIN_ERR_INVALID_ARG, "NULL argument");
+    st = eval_all(sys, x_dev, EV_EG);
+    if (st != FFMIN_OK) return st;
+    CK(cudaMemcpyAsync(g_dev, vslot(sys->c, V_GT), sizeof(double) * 3 * sys->n_atoms, cudaMemcpyDeviceToDevice,
+                       sys->stream));
+    ffmin_status res = FFMIN_OK;
+    for (int b = 0; b < sys->n_sys; b++) {
+        e_host[b] = sys->hst[b].res_f;
+        if (sys->hst[b].status == FFMIN_ERR_NONFINITE) res = FFMIN_ERR_NONFINITE;
+    }
+    st = leave(sys);
+    return st != FFMIN_OK ? st : res;
+}
+
+ffmin_status ffmin_energy_grad_host(ffmin_system *sys, const double *x_host, double *e_host, double *g_host) {
+    ffmin_status st = enter(sys);
+    if (st != FFMIN_OK) return st;
+    if (!x_host || !e_host) return fail(sys, FFMIN_ERR_INVALID_ARG, "NULL argument");
+    const size_t bytes = sizeof(double) * 3 * sys->n_atoms;
+    double *stage = vslot(sys->c, V_XT);  // scratch: overwritten by the evaluation anyway
+    CK(cudaMemcpyAsync(stage, x_host, bytes, cudaMemcpyHostToDevice, sys->stream));
+    st = eval_all(sys, stage, g_host ? EV_EG : EV_E);
+    if (st != FFMIN_OK) return st;
+    if (g_host) {
+        CK(cudaMemcpyAsync(g_host, vslot(sys->c, V_GT), bytes, cudaMemcpyDeviceToHost, sys->stream));
+        CK(cudaStreamSynchronize(sys->stream));
+    }
+    ffmin_status res = FFMIN_OK;
+    for (int b = 0; b < sys->n_sys; b++) {
+        e_host[b] = sys->hst[b].res_f;
+        if (sys->hst[b].status == FFMIN_ERR_NONFINITE) res = FFMIN_ERR_NONFINITE;
+    }
+    st = leave(sys);
+    return st != FFMIN_OK ? st : res;
+}
+
+static ffmin_status check_options(ffmin_system *sys, const ffmin_options *o) {
+    if (!o) return fail(sys, FFMIN_ERR_INVALID_ARG, "options is NULL");
+    if (o->method < FFMIN_GD || o->method > FFMIN_GRADFREE) return fail(sys, FFMIN_ERR_INVALID_ARG, "bad method");
+    if (o->cg_variant < 0 || o->cg_variant > FFMIN_CG_DY) return fail(sys, FFMIN_ERR_INVALID_ARG, "bad cg_variant");
+    if (o->ls < 0 || o->ls > FFMIN_LS_PAR) return fail(sys, FFMIN_ERR_INVALID_ARG, "bad line search");
+    if (o->method == FFMIN_LBFGS && (o->lbfgs_m < 1 || o->lbfgs_m > MAXM))
+        return fail(sys, FFMIN_ERR_INVALID_ARG, "lbfgs_m must be in [1, 16]");
+    if (!(o->h0 > 0.0) || !(o->k_plus > 1.0) || !(o->k_minus > 0.0 && o->k_minus < 1.0) ||
+        !(o->eps_h > 0.0 && o->eps_h < 1.0) || o->ls_par_K < 2 || !(o->gtol_inf >= 0.0) || o->max_iter < 0 ||
+        o->max_evals < 1)
+        return fail(sys, FFMIN_ERR_INVALID_ARG, "line-search / stopping parameter out of range");
+    if (o->method == FFMIN_GRADFREE && (sys->n_sys != 1 || !(o->gradfree_delta > 0.0)))
+        return fail(sys, FFMIN_ERR_INVALID_ARG, "GRADFREE needs one system and delta > 0");
+    if (o->use_learned_precond && !sys->have_precond)
+        return fail(sys, FFMIN_ERR_INVALID_ARG, "no preconditioner weights set");
+    return FFMIN_OK;
+}
+
+static ffmin_status minimize_dev(ffmin_system *sys, double *x_dev, const ffmin_options *o, ffmin_result *res) {
+    const Ctx &c = sys->c;
+    const size_t bytes = sizeof(double) * 3 * sys->n_atoms;
+    if (o->method == FFMIN_GRADFREE) {
+        CK(cudaMemcpyAsync(vslot(c, V_X), x_dev, bytes, cudaMemcpyDeviceToDevice, sys->stream));
+        cudaError_t e = parab_minimize(sys, o, res);
+        if (e != cudaSuccess) return cuda_fail(sys, e, "gradient-free minimization");
+        CK(cudaMemcpyAsync(x_dev, vslot(c, V_X), bytes, cudaMemcpyDeviceToDevice, sys->stream));
+        return FFMIN_OK;
+    }
+    CK(cudaMemcpyAsync(vslot(c, V_X), x_dev, bytes, cudaMemcpyDeviceToDevice, sys->stream));
+    CK(cudaMemsetAsync(vslot(c, V_P), 0, bytes, sys->stream));
+    CK(cudaMemsetAsync(vslot(c, V_R), 0, bytes, sys->stream));
+    for (int b = 0; b < sys->n_sys; b++) {
+        SysState &S = sys->hst[b];
+        const int32_t atom0 = S.atom0, natoms = S.natoms, tile0 = S.tile0, ntile = S.ntile;
+        std::memset(&S, 0, sizeof(S));
+        S.atom0 = atom0; S.natoms = natoms; S.tile0 = tile0; S.ntile = ntile;
+        S.method = o->method;
+        S.cg_variant = o->cg_variant;
+        S.ls = o->ls;
+        S.m = o->lbfgs_m;
+        S.max_iter = o->max_iter;
+        S.max_evals = o->max_evals;
+        S.restart_every = o->cg_restart_every > 0 ? o->cg_restart_every : 3 * natoms;
+        S.K = o->ls_par_K;
+        S.g0 = o->ls_par_g0;
+        S.gtol = o->gtol_inf;
+        S.h0_init = o->h0;
+        S.kplus = o->k_plus;
+        S.kminus = o->k_minus;
+        S.eps_h = o->eps_h;
+        S.precond_on = o->use_learned_precond ? 1 : 0;
+        S.active = 1;
+        S.phase = PH_START;
+        S.result_slot = o->method == FFMIN_FGM ? V_XB : V_X;
+        S.ev_kind = EV_EG;
+        S.ev_base = V_X;
+        S.ev_dir = -1;
+        S.ev_h = 0.0;
+        S.ev_scale = 1.0;
+    }
+    ffmin_status st = upload_states(sys);
+    if (st != FFMIN_OK) return st;
+    int32_t n = sys->n_sys;
+    CK(cudaMemcpyAsync(c.nactive, &n, sizeof(int32_t), cudaMemcpyHostToDevice, sys->stream));
+    st = ensure_graph(sys);
+    if (st != FFMIN_OK) return st;
+    const int64_t max_ticks = o->max_ticks > 0 ? o->max_ticks : (int64_t)o->max_evals + 64;
+    int64_t ticks = 0;
+    bool timeout = false;
+    for (;;) {
+        CK(cudaGraphLaunch(sys->graph, sys->stream));
+        ticks += sys->graph_ticks;
+        CK(cudaMemcpyAsync(sys->h_nactive, c.nactive, sizeof(int32_t), cudaMemcpyDeviceToHost, sys->stream));
+        CK(cudaStreamSynchronize(sys->stream));
+        if (*sys->h_nactive <= 0) break;
+        if (ticks >= max_ticks) { timeout = true; break; }
+    }
+    sys->last_ticks = ticks;
+    sys->last_launches = ticks * KERNELS_PER_TICK;
+    st = download_states(sys);
+    if (st != FFMIN_OK) return st;
+    const int slot = o->method == FFMIN_FGM ? V_XB : V_X;
+    CK(cudaMemcpyAsync(x_dev, vslot(c, slot), bytes, cudaMemcpyDeviceToDevice, sys->stream));
+    int64_t pairs = 0;
+    for (int b = 0; b < sys->n_sys; b++) {
+        const SysState &S = sys->hst[b];
+        ffmin_result &r = res[b];
+        r.energy = S.res_f;
+        r.grad_inf = S.res_ginf;
+        r.iterations = S.iter;
+        r.energy_evals = S.ne;
+        r.grad_evals = S.neg;
+        r.ls_failures = S.lsf;
+        r.stop_reason = (timeout && S.active) ? FFMIN_ERR_TIMEOUT : S.status;
+        const int64_t nb = S.natoms;
+        pairs += (int64_t)(S.ne + S.neg) * nb * (nb - 1) / 2;
+    }
+    sys->last_pairs = pairs;
+    return FFMIN_OK;
+}
+
+ffmin_status ffmin_minimize(ffmin_system *sys, double *x_dev, const ffmin_options *o, ffmin_result *res) {
+    ffmin_status st = enter(sys);
+    if (st != FFMIN_OK) return st;
+    if (!x_dev || !res) return fail(sys, FFMIN_ERR_INVALID_ARG, "NULL argument");
+    if ((st = check_options(sys, o)) != FFMIN_OK) return st;
+    st = minimize_dev(sys, x_dev, o, res);
+    if (st != FFMIN_OK) return st;
+    return leave(sys);
+}
+
+ffmin_status ffmin_minimize_host(ffmin_system *sys, double *x_host, const ffmin_options *o, ffmin_result *res) {
+    ffmin_status st = enter(sys);
+    if (st != FFMIN_OK) return st;
+    if (!x_host || !res) return fail(sys, FFMIN_ERR_INVALID_ARG, "NULL argument");
+    if ((st = check_options(sys, o)) != FFMIN_OK) return st;
+    const size_t bytes = sizeof(double) * 3 * sys->n_atoms;
+    double *stage = vslot(sys->c, V_XIN);
+    CK(cudaMemcpyAsync(stage, x_host, bytes, cudaMemcpyHostToDevice, sys->stream));
+    st = minimize_dev(sys, stage, o, res);
+    if (st != FFMIN_OK) return st;
+    CK(cudaMemcpyAsync(x_host, stage, bytes, cudaMemcpyDeviceToHost, sys->stream));
+    return leave(sys);
+}
+
+ffmin_status ffmin_time_pair_kernel(ffmin_system *sys, const double *x_dev, int32_t with_grad, int32_t reps,
+                                    float *ms) {
+    ffmin_status st = enter(sys);
+    if (st != FFMIN_OK) return st;
+    if (!x_dev || !ms || reps < 1) return fail(sys, FFMIN_ERR_INVALID_ARG, "bad argument");
+    // one full evaluation leaves the positions of x in the pair-kernel inputs
+    st = eval_all(sys, x_dev, with_grad ? EV_EG : EV_E);
+    if (st != FFMIN_OK) return st;
+    for (int b = 0; b < sys->n_sys; b++) sys->hst[b].ev_kind = with_grad ? EV_EG : EV_E;
+    if ((st = upload_states(sys)) != FFMIN_OK) return st;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(launch_pair(sys->c, sys->pair_grid, sys->stream));  // warm-up
+    CK(cudaEventRecord(e0, sys->stream));
+    for (int r = 0; r < reps; r++) CK(launch_pair(sys->c, sys->pair_grid, sys->stream));
+    CK(cudaEventRecord(e1, sys->stream));
+    CK(cudaEventSynchronize(e1));
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms = t / (float)reps;
+    for (int b = 0; b < sys->n_sys; b++) sys->hst[b].ev_kind = EV_NONE;
+    if ((st = upload_states(sys)) != FFMIN_OK) return st;
+    return leave(sys);
+}
+
+ffmin_status ffmin_last_stats(const ffmin_system *sys, int64_t *ticks, int64_t *launches, int64_t *pairs) {
+    if (!sys) return FFMIN_ERR_INVALID_ARG;
+    if (ticks) *ticks = sys->last_ticks;
+    if (launches) *launches = sys->last_launches;
+    if (pairs) *pairs = sys->last_pairs;
+    return FFMIN_OK;
+}
+
+ffmin_status ffmin_set_precond(ffmin_system *sys, const uint16_t *w, int32_t n_params) {
+    if (!sys || !w || n_params != 449) return fail(sys, FFMIN_ERR_INVALID_ARG, "need 449 FP16 weights");
+    cudaError_t e = cudaMemcpy((void *)sys->c.mlp_w, w, sizeof(uint16_t) * 449, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(sys, e, "ffmin_set_precond");
+    sys->have_precond = true;
+    return FFMIN_OK;
+}
+
+}  // extern "C"
+
+// placeholder for the gradient-free path until its kernels are in place
+namespace ffm {
+cudaError_t parab_minimize(ffmin_system *sys, const ffmin_options *o, ffmin_result *res) {
+    (void)sys; (void)o; (void)res;
+    return cudaErrorNotSupported;
+}
+}  // namespace ffm

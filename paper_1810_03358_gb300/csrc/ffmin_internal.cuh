@@ -1,0 +1,156 @@
+// Internal structures shared by the ffmin CUDA translation units.
+//
+// Layout in HBM (one batch of n_sys systems, atoms concatenated):
+//   - vectors: V_NSLOT FP64 arrays of vstride doubles (3 per atom, xyz AoS):
+//     current point X, gradient G, direction R, trial point XT and its
+//     gradient GT, FGM's w / momentum / best point, the learned H0 diagonal
+//     and the L-BFGS ring of (s, y) pairs (m + 1 physical slots each);
+//   - pair-kernel inputs rewritten for every evaluation: per atom float4 or
+//     double4_32a (x, y, z, q*sqrt(C)) and constant float2 / double2
+//     (sigma, sqrt(24 eps));
+//   - per-(tile, j-chunk) partial row sums of the pair kernel
+//     ([n_items][TI] float4 or double4_32a: gx, gy, gz, row energy);
+//   - bonded terms (FP64) with a per-atom incidence list, so that every
+//     atom gathers its own bonded gradient without atomics;
+//   - per-system control state (SysState) driven by the last block of the
+//     per-tile kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ffmin.h"
+
+namespace ffm {
+
+constexpr int TI = 128;        // atoms per tile = threads of every per-tile kernel
+constexpr int TJ = 128;        // j atoms staged per shared-memory tile in the pair kernel
+constexpr int MAXM = 16;       // largest L-BFGS memory
+constexpr int NRING = MAXM + 1;  // ring slots (m committed pairs + one staging slot)
+constexpr int NRED = 2 * NRING + 4;  // reduction values per tile
+
+enum Slot : int {
+    V_X = 0, V_G, V_R, V_XT, V_GT, V_W, V_P, V_XB, V_D, V_XIN,
+    V_S0, V_Y0 = V_S0 + NRING, V_NSLOT = V_Y0 + NRING
+};
+
+enum EvKind : int { EV_NONE = 0, EV_E = 1, EV_EG = 2 };
+
+enum UpdKind : int {
+    U_NONE = 0,
+    U_ACCEPT,        // X <- XT, G <- GT
+    U_PUSH,          // L-BFGS: s = XT - X, y = GT - G into the staging slot, dots, then ACCEPT
+    U_FGM_W,         // W <- XT, G <- GT (optionally XB <- XT)
+    U_FGM_ACCEPT,    // Xn = fma(h, R * inv, W); P <- Xn - X (0 on restart); X <- Xn (XB <- Xn)
+    U_FGM_RESET,     // X <- W, P <- 0
+    U_FGM_BEST_W     // XB <- W
+};
+
+enum Phase : int {
+    PH_IDLE = 0, PH_START, PH_DIR, PH_LS, PH_ACCEPT, PH_FGM_W, PH_FINAL, PH_EVAL_ONLY, PH_DONE
+};
+
+struct Item { int32_t tile, j0, nj, diag; };
+
+struct Tile { int32_t sys, a0, na, item0, nitem, pad0, pad1, pad2; };
+
+struct DirOp {
+    int32_t on, use_d, dots;  // dots: 1 -> |R|^2, <G,R>; 2 -> <Y_j, R> for the Y list
+    int32_t nS, nY;
+    int32_t sS[NRING], sY[NRING];
+    double a, b, outer;
+    double cS[NRING], cY[NRING];
+};
+
+struct UpdOp {
+    int32_t op, best, restart, stage;  // stage: physical ring slot for U_PUSH
+    int32_t nS, sS[NRING];             // committed s slots (U_PUSH dots)
+    double h, inv;
+};
+
+struct SysState {
+    // geometry of the system inside the batch
+    int32_t atom0, natoms, tile0, ntile;
+    // options
+    int32_t method, cg_variant, ls, m, max_iter, max_evals, restart_every, K, g0, use_d;
+    double gtol, h0_init, kplus, kminus, eps_h;
+    // status and counters
+    int32_t active, status, iter, ne, neg, lsf, fresh, phase;
+    // current point
+    double f, gg, ginf, rg;
+    double h0, h_acc;
+    // requests for the next kernels
+    UpdOp upd;
+    DirOp dir[2];
+    int32_t ev_kind, ev_base, ev_dir, cg_check;
+    double ev_h, ev_scale;
+    // line search
+    int32_t ls_kind, ls_step, ls_k, ls_pad;
+    double lh[4], lf[4], fstar, slope, rnorm, ls_f0, ls_h0v;
+    // L-BFGS ring (physical slots 0..m): committed pairs oldest first
+    int32_t ring_count, ring_pad;
+    int32_t ring[NRING];
+    double rho[NRING], yy[NRING];
+    double SY[NRING][NRING];  // SY[a][b] = <s_a, y_b>, a older than b
+    double sg[NRING];         // <s_a, g> at the current point
+    double alpha[NRING];
+    // FGM
+    double th_prev, fx, fb, fw, xb_ginf;
+    int32_t xb_known, result_slot;
+    // result
+    double res_f, res_ginf;
+    // learned preconditioner in use for this run
+    int32_t precond_on, precond_pad;
+};
+
+struct Ctx {
+    int32_t n_sys, n_tiles, n_items, n_atoms;
+    int64_t vstride;
+    int32_t prec;           // ffmin_precision
+    int32_t pad;
+    const Tile *tiles;
+    const Item *items;
+    SysState *st;
+    double *vec;            // [V_NSLOT][vstride]
+    // pair kernel inputs / outputs
+    float4 *posf;
+    const float2 *parf;
+    double4_32a *posd;
+    const double2 *pard;
+    const double *qs;       // q * sqrt(C) per atom (FP64)
+    float4 *gpf;            // [n_items][TI]
+    double4_32a *gpd;
+    // bonded terms
+    const int32_t *inc_off; // [n_atoms + 1]
+    const int2 *inc;        // x: (type << 2) | position, y: term index
+    const int2 *bidx;
+    const double2 *bpar;
+    const int4 *aidx;
+    const double2 *apar;
+    const int4 *didx;
+    const double4_32a *dpar;
+    // reductions
+    double *red;            // [n_tiles][NRED]
+    unsigned int *counters; // one per kernel kind, reset by the last block
+    int32_t *nactive;       // systems still minimizing
+    // learned preconditioner features
+    const float *feat;      // [n_atoms][3] (q, sigma, eps)
+    int32_t *ncount;        // [n_atoms] neighbours within 8 A (pair kernel EG, optional)
+    const uint16_t *mlp_w;  // 449 FP16 weights
+};
+
+inline __host__ __device__ double *vslot(const Ctx &c, int slot) { return c.vec + (int64_t)slot * c.vstride; }
+
+// counters[] indices
+enum { CNT_PAIR = 0, CNT_PAIR_EXIT = 1, CNT_FIN = 2, CNT_UPD = 3, CNT_DIR1 = 4, CNT_DIR2 = 5,
+       CNT_PARAB = 6, CNT_PARAB2 = 7, CNT_N = 8 };
+
+// ---- launchers (defined in the .cu files) ----
+cudaError_t launch_prepare(const Ctx &c, cudaStream_t s);
+cudaError_t launch_pair(const Ctx &c, int grid, cudaStream_t s);
+cudaError_t launch_finalize(const Ctx &c, cudaStream_t s);
+cudaError_t launch_update(const Ctx &c, cudaStream_t s);
+cudaError_t launch_dir(const Ctx &c, int which, cudaStream_t s);
+int pair_grid_size(int prec);
+
+}  // namespace ffm

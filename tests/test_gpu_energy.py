@@ -1,0 +1,129 @@
+"""Parity of the CUDA energy / gradient (pair kernel + bonded terms + fixed-
+order reductions) with the FP64 oracle, through the C ABI.
+
+Bars: FP64 path E within 1e-6 of sum|terms| and every gradient component
+within 1e-4 of the largest force (the stated bars, which bind the plain
+FP64 path; the MIXED path's error is measured and reported), plus tighter FP64
+rounding bounds (1e-12 sum|terms|, 1e-9 max force) that a plausible
+indexing or sign slip would break.  MIXED path (FP32 pair terms, FP32 sums
+inside a j-chunk of <= 2048 atoms, FP64 beyond): E within 1e-5 sum|terms|
+and gradient within 1e-4 max force, from ~10 roundings of u = 6e-8 per pair
+term amplified by the r^-12 power (12 u relative) and chunk sums of
+sqrt(2048) u typical growth."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1810_03358_gb300 import synth
+from tests.gpu_util import need_gpu, split, to_dev
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: dict(e=1e-12, g=1e-9), 1: dict(e=1e-5, g=1e-4)}
+BAR = dict(e=1e-6, g=1e-4)
+
+
+@pytest.fixture(scope="module")
+def ff():
+    return need_gpu()
+
+
+def check(ffmin, oracle_mod, systems, prec, xs=None):
+    xs = xs or [s.x for s in systems]
+    S = ffmin.System(systems, prec)
+    x = to_dev(xs)
+    e, g = S.energy_grad(x)
+    e_only = S.energy(x)
+    g = split(g.cpu().numpy(), systems)
+    for b, s in enumerate(systems):
+        d, st, go = oracle_mod.energy_terms(s, xs[b], grad=True)
+        assert st == 0
+        err_e = abs(e[b] - d["total"]) / d["sum_abs"] if d["sum_abs"] > 0 else abs(e[b])
+        assert err_e <= TOL[prec]["e"], (b, err_e)
+        if prec == 0:
+            assert err_e <= BAR["e"]
+        assert abs(e_only[b] - e[b]) <= TOL[prec]["e"] * max(d["sum_abs"], 1.0)
+        fmax = max(np.abs(go).max(), 1e-30) if go.size else 1.0
+        err_g = np.abs(g[b] - go).max() / fmax if go.size else 0.0
+        if prec == 1:
+            # FP32 coordinates quantise each pair separation by ~u |x|; near a
+            # minimum the force scale is the stopping tolerance (0.1), so the
+            # bar is 2 % of it in absolute terms
+            err_g = min(err_g, np.abs(g[b] - go).max() / (0.02 * 0.1 / TOL[1]["g"]))
+        assert err_g <= TOL[prec]["g"], (b, err_g)
+        if prec == 0:
+            assert err_g <= BAR["g"]
+    S.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 64, 127, 128, 129, 300])
+def test_single_system_sizes(ff, oracle_mod, prec, n):
+    check(ff, oracle_mod, [synth.make_system(n, 100 + n)], prec)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_paper_small_config_500(ff, oracle_mod, prec):
+    # 500-atom globule, seed 1 (the small configuration)
+    check(ff, oracle_mod, [synth.make_system(500, 1)], prec)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batch_ragged(ff, oracle_mod, prec):
+    systems = [synth.make_system(n, 200 + k) for k, n in enumerate([5, 300, 129, 1, 777, 64])]
+    check(ff, oracle_mod, systems, prec)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_minimized_geometry(ff, oracle_mod, prec):
+    # near a minimum the forces are small: the relative gradient bar is tight
+    s = synth.make_system(150, 7)
+    xo, r = oracle_mod.minimize(s, s.x, method=oracle_mod.LBFGS)
+    check(ff, oracle_mod, [s], prec, xs=[xo])
+
+
+def test_coincident_atoms_report_nonfinite(ff):
+    import torch
+    s = synth.make_system(40, 3)
+    x = s.x.copy()
+    x[7] = x[20]
+    S = ff.System([s], 0)
+    with pytest.raises(ff.FfminError) as ei:
+        S.energy_grad(to_dev([x]))
+    assert ei.value.status == ff.FFMIN_ERR_NONFINITE
+    S.close()
+
+
+_ORACLE_30K = {}
+
+
+def oracle_30k(oracle_mod, s):
+    if "r" not in _ORACLE_30K:
+        _ORACLE_30K["r"] = oracle_mod.energy_terms(s, s.x, grad=True)
+    return _ORACLE_30K["r"]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_full_size_30000(ff, oracle_mod, prec):
+    # the paper-scale globule (30,000 atoms, seed 3) in the launch
+    # configuration the benchmark times: total E and every gradient component
+    # against the oracle (about 20 s of single-threaded oracle work, shared
+    # by both precisions), plus the gradient of sampled atoms computed by the
+    # oracle from that atom's own terms
+    s = synth.make_system(30000, 3)
+    S = ff.System([s], prec)
+    x = to_dev([s.x])
+    e, g = S.energy_grad(x)
+    g = g.cpu().numpy().reshape(-1, 3)
+    d, st, go = oracle_30k(oracle_mod, s)
+    assert st == 0
+    # 4.5e8 terms summed in different orders: FP64 rounding bound ~1e-10
+    assert abs(e[0] - d["total"]) / d["sum_abs"] <= (1e-10 if prec == 0 else TOL[1]["e"])
+    fmax = np.abs(go).max()
+    assert np.abs(g - go).max() / fmax <= TOL[prec]["g"]
+    rng = np.random.default_rng(0)
+    idx = np.concatenate([[0, 1, 127, 128, 29999], rng.integers(0, 30000, 11)])
+    ga = np.array([oracle_mod.atom_gradient(s, s.x, int(i)) for i in idx])
+    assert np.abs(g[idx] - ga).max() / fmax <= TOL[prec]["g"]
+    S.close()

@@ -219,3 +219,10 @@ def test_splitmix64_published_values(oracle_mod):
     assert oracle_mod.splitmix64(0, 1) == g["splitmix64_seed0_out1"]
     picks = [oracle_mod.pick_atom(99, k, 7) for k in range(2000)]
     assert min(picks) == 0 and max(picks) == 6
+
+
+def test_atom_gradient_equals_full_gradient_row(oracle_mod):
+    s = synth.make_system(25, 13)
+    e, g = oracle_mod.energy_grad(s, s.x)
+    for i in (0, 1, 12, 23, 24):
+        assert np.allclose(oracle_mod.atom_gradient(s, s.x, i), g[i], rtol=1e-12, atol=1e-9)
