@@ -296,12 +296,45 @@ def bench_reference(args):
 
 
 def profile_run(args):
-    """Small fixed workload for ncu captures: one E + grad E of the
-    30,000-atom globule with the MIXED pair kernel, then one with FP64."""
+    """Small fixed workloads for ncu captures.  Default: one E + grad E of
+    the 30,000-atom globule with the MIXED pair kernel, then one with FP64.
+    --profile-minimize K: a K-step MIXED L-BFGS run of the 3,334-atom globule
+    (every kernel of the minimizer pipeline)."""
     import torch
     from paper_1810_03358_gb300 import build as gbuild
     gbuild.build()
     from paper_1810_03358_gb300 import ffmin, synth
+    if args.profile_batch:
+        systems = synth.make_batch(256)
+        S = ffmin.System(systems, ffmin.FFMIN_MIXED)
+        x = torch.tensor([v for s in systems for v in s.x.reshape(-1)], dtype=torch.float64, device="cuda")
+        S.minimize(x.clone(), method="LBFGS", max_iter=1)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        r = S.minimize(x.clone(), method="LBFGS", max_iter=args.profile_batch)
+        ev1.record()
+        torch.cuda.synchronize()
+        st = S.last_stats()
+        print("profile-batch", st, "ms", ev0.elapsed_time(ev1), "ms/tick", ev0.elapsed_time(ev1) / st["ticks"])
+        S.close()
+        return
+    if args.profile_minimize:
+        s = synth.make_system(3334, 2)
+        x = torch.tensor(s.x.reshape(-1), dtype=torch.float64, device="cuda")
+        S = ffmin.System([s], ffmin.FFMIN_MIXED)
+        S.minimize(x.clone(), method="LBFGS", max_iter=2)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        r = S.minimize(x.clone(), method="LBFGS", max_iter=args.profile_minimize)
+        ev1.record()
+        torch.cuda.synchronize()
+        st = S.last_stats()
+        print("profile-minimize", r[0]["iterations"], st, "ms", ev0.elapsed_time(ev1),
+              "ms/tick", ev0.elapsed_time(ev1) / st["ticks"])
+        S.close()
+        return
     s = synth.make_system(args.profile_atoms, SEED)
     x = torch.tensor(s.x.reshape(-1), dtype=torch.float64, device="cuda")
     for prec in (ffmin.FFMIN_MIXED, ffmin.FFMIN_FP64):
@@ -321,6 +354,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true", help="small fixed workload for ncu")
     ap.add_argument("--profile-atoms", type=int, default=N_ATOMS)
+    ap.add_argument("--profile-minimize", type=int, default=0)
+    ap.add_argument("--profile-batch", type=int, default=0)
     args = ap.parse_args()
     if args.profile:
         profile_run(args)

@@ -17,8 +17,15 @@
 using namespace ffm;
 
 namespace ffm {
-cudaError_t parab_minimize(ffmin_system *sys, const ffmin_options *o, ffmin_result *res);
-}
+struct ParabState;
+cudaError_t launch_parab_move(const Ctx &c, ParabState *ps, int grid, cudaStream_t s);
+size_t parab_state_bytes();
+void parab_state_init(void *host_buf, int n, int atom0, int mode, int max_moves, uint64_t seed,
+                      double delta);
+size_t parab_offset_move();
+size_t parab_offset_stop();
+}  // namespace ffm
+static ffmin_status parab_minimize(ffmin_system *sys, const ffmin_options *o, ffmin_result *res);
 
 struct ffmin_system {
     int n_sys = 0;
@@ -34,10 +41,14 @@ struct ffmin_system {
     std::vector<int64_t> atom_off;
     std::vector<int32_t> sys_natoms;
     std::vector<SysState> hst;
-    int pair_grid = 0;
+    int grid32 = 0, grid64 = 0;
     int graph_ticks = 0;
     cudaGraphExec_t graph = nullptr;
     int32_t *h_nactive = nullptr;  // pinned
+    // gradient-free path: device state and a graph of PARAB_MOVES moves
+    void *parab_state = nullptr;
+    cudaGraphExec_t parab_graph = nullptr;
+    int parab_grid = 0;
     // learned preconditioner
     bool have_precond = false;
     // stats of the last minimize
@@ -140,6 +151,7 @@ ffmin_status ffmin_destroy(ffmin_system *sys) {
     if (!sys) return FFMIN_ERR_INVALID_ARG;
     if (sys->stream) cudaStreamSynchronize(sys->stream);
     if (sys->graph) cudaGraphExecDestroy(sys->graph);
+    if (sys->parab_graph) cudaGraphExecDestroy(sys->parab_graph);
     for (void *p : sys->allocs) cudaFree(p);
     if (sys->h_nactive) cudaFreeHost(sys->h_nactive);
     if (sys->ev_in) cudaEventDestroy(sys->ev_in);
@@ -156,9 +168,10 @@ static bool idx_ok(const int32_t *idx, int64_t count, int32_t n) {
 }
 
 // j-chunk length of a system: a multiple of TJ, chosen so that the whole
-// batch exposes at least ~4 work items per resident pair-kernel block
+// batch exposes ~10 work items per resident pair-kernel block (the queue's
+// tail then costs at most a tenth of a block's share)
 static int chunk_len(int32_t n, int64_t total_tiles, int grid) {
-    int64_t want_items = 4LL * grid;
+    int64_t want_items = 10LL * grid;
     int64_t chunks = std::max<int64_t>(1, (want_items + total_tiles - 1) / std::max<int64_t>(total_tiles, 1));
     int64_t len = (n + chunks - 1) / chunks;
     len = ((len + TJ - 1) / TJ) * TJ;
@@ -207,7 +220,9 @@ ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t pre
         ffmin_destroy(sys);
         return fail(nullptr, FFMIN_ERR_OOM, "pinned allocation failed");
     }
-    sys->pair_grid = pair_grid_size(precision);
+    sys->grid32 = pair_grid_size(0);
+    sys->grid64 = pair_grid_size(1);
+    const int chunk_grid = precision == FFMIN_MIXED ? sys->grid32 : sys->grid64;
 
     // ---- tiles, items, per-atom data, bonded terms ----
     std::vector<Tile> tiles;
@@ -268,7 +283,7 @@ ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t pre
         }
         // tiles and (tile, j-chunk) items
         tile0[b] = (int)tiles.size();
-        const int L = chunk_len(t.n_atoms, total_tiles, sys->pair_grid);
+        const int L = chunk_len(t.n_atoms, total_tiles, chunk_grid);
         for (int a0 = 0; a0 < t.n_atoms; a0 += TI) {
             Tile tl{};
             tl.sys = b;
@@ -290,6 +305,31 @@ ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t pre
         }
         ntile[b] = (int)tiles.size() - tile0[b];
     }
+    // bonded work items go first in the queue: they are latency-bound FP64
+    // work and overlap with the FP32 pair items that follow
+    const int n_terms = (int)(bidx.size() + aidx.size() + didx.size());
+    std::vector<int32_t> term_sys(std::max(n_terms, 1), 0);
+    {
+        int t = 0;
+        for (int b = 0; b < n_sys; b++) for (int k = 0; k < tops[b].n_bonds; k++) (void)k, term_sys[t++] = b;
+        for (int b = 0; b < n_sys; b++) for (int k = 0; k < tops[b].n_angles; k++) (void)k, term_sys[t++] = b;
+        for (int b = 0; b < n_sys; b++) for (int k = 0; k < tops[b].n_dihedrals; k++) (void)k, term_sys[t++] = b;
+    }
+    const int n_bitems = (n_terms + BONDED_ITEM_TERMS - 1) / BONDED_ITEM_TERMS;
+    {
+        std::vector<Item> all;
+        all.reserve(items.size() + n_bitems);
+        for (int k = 0; k < n_bitems; k++) {
+            Item it{};
+            it.tile = -1;
+            it.j0 = k * BONDED_ITEM_TERMS;
+            it.nj = std::min(BONDED_ITEM_TERMS, n_terms - it.j0);
+            all.push_back(it);
+        }
+        for (const Item &it : items) all.push_back(it);
+        for (Tile &tl : tiles) tl.item0 += n_bitems;
+        items.swap(all);
+    }
     std::vector<int32_t> inc_off(total + 1, 0);
     std::vector<int2> inc;
     for (int64_t a = 0; a < total; a++) {
@@ -303,6 +343,14 @@ ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t pre
     c.n_sys = n_sys;
     c.n_tiles = (int)tiles.size();
     c.n_items = (int)items.size();
+    c.n_pair_items = (int)items.size() - n_bitems;
+    // no more resident blocks than work items: idle blocks would only pay
+    // for queue atomics
+    sys->grid32 = std::max(1, std::min(sys->grid32, c.n_items));
+    sys->grid64 = std::max(1, std::min(sys->grid64, c.n_items));
+    c.n_bonds = (int)bidx.size();
+    c.n_angles = (int)aidx.size();
+    c.n_terms = n_terms;
     c.n_atoms = (int)total;
     c.vstride = ((3 * total + 31) / 32) * 32;
     c.prec = precision;
@@ -329,18 +377,22 @@ ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t pre
     double *d_qs;
     CKC(upload(sys, &d_qs, qs));
     c.qs = d_qs;
-    if (precision == FFMIN_MIXED) {
-        float2 *d_parf;
-        CKC(dalloc(sys, &c.posf, total));
-        CKC(upload(sys, &d_parf, parf));
-        c.parf = d_parf;
-        CKC(dalloc(sys, &c.gpf, (size_t)c.n_items * TI));
-    } else {
+    {
+        // FP64 pair inputs always; FP32 ones too for MIXED objects, whose
+        // runs start with FP32 pair terms and finish with FP64 ones
         double2 *d_pard;
         CKC(dalloc(sys, &c.posd, total));
         CKC(upload(sys, &d_pard, pard));
         c.pard = d_pard;
         CKC(dalloc(sys, &c.gpd, (size_t)c.n_items * TI));
+        if (precision == FFMIN_MIXED) {
+            float2 *d_parf;
+            CKC(dalloc(sys, &c.posf, total));
+            CKC(dalloc(sys, &c.dispf, total));
+            CKC(upload(sys, &d_parf, parf));
+            c.parf = d_parf;
+            CKC(dalloc(sys, &c.gpf, (size_t)c.n_items * TI));
+        }
     }
     int32_t *d_inc_off; int2 *d_inc, *d_bidx; double2 *d_bpar, *d_apar; int4 *d_aidx, *d_didx; double4_32a *d_dpar;
     CKC(upload(sys, &d_inc_off, inc_off));
@@ -353,9 +405,15 @@ ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t pre
     CKC(upload(sys, &d_dpar, dpar));
     c.inc_off = d_inc_off; c.inc = d_inc; c.bidx = d_bidx; c.bpar = d_bpar;
     c.aidx = d_aidx; c.apar = d_apar; c.didx = d_didx; c.dpar = d_dpar;
+    int32_t *d_term_sys;
+    CKC(upload(sys, &d_term_sys, term_sys));
+    c.term_sys = d_term_sys;
+    CKC(dalloc(sys, &c.te, std::max(n_terms, 1)));
+    CKC(dalloc(sys, &c.tg, 3 * (2 * bidx.size() + 3 * aidx.size() + 4 * didx.size()) + 3));
     CKC(dalloc(sys, &c.red, (size_t)c.n_tiles * NRED));
     CKC(dalloc(sys, &c.counters, CNT_N));
     CKC(dalloc(sys, &c.nactive, 1));
+    CKC(dalloc(sys, &c.nmode, 2));
     float *d_feat;
     CKC(upload(sys, &d_feat, feat));
     c.feat = d_feat;
@@ -374,6 +432,8 @@ ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t pre
         S.natoms = tops[b].n_atoms;
         S.tile0 = tile0[b];
         S.ntile = ntile[b];
+        S.mixed = precision == FFMIN_MIXED ? 1 : 0;
+        S.mode = precision == FFMIN_MIXED ? 0 : 1;
         sys->sys_natoms[b] = tops[b].n_atoms;
     }
     CKC(cudaMemcpyAsync(d_st, sys->hst.data(), sizeof(SysState) * n_sys, cudaMemcpyHostToDevice, sys->stream));
@@ -416,6 +476,16 @@ static ffmin_status download_states(ffmin_system *sys) {
     return FFMIN_OK;
 }
 
+// active-system counters read by the kernels: all systems start in the
+// object's precision mode (FP32 for MIXED, FP64 otherwise)
+static ffmin_status set_counts(ffmin_system *sys) {
+    int32_t h[3] = {sys->n_sys, 0, 0};
+    h[sys->prec == FFMIN_MIXED ? 1 : 2] = sys->n_sys;
+    CK(cudaMemcpyAsync(sys->c.nactive, &h[0], sizeof(int32_t), cudaMemcpyHostToDevice, sys->stream));
+    CK(cudaMemcpyAsync(sys->c.nmode, &h[1], 2 * sizeof(int32_t), cudaMemcpyHostToDevice, sys->stream));
+    return FFMIN_OK;
+}
+
 static cudaError_t launch_tick(ffmin_system *sys) {
     const Ctx &c = sys->c;
     cudaError_t e;
@@ -423,12 +493,12 @@ static cudaError_t launch_tick(ffmin_system *sys) {
     if ((e = launch_dir(c, 0, sys->stream)) != cudaSuccess) return e;
     if ((e = launch_dir(c, 1, sys->stream)) != cudaSuccess) return e;
     if ((e = launch_prepare(c, sys->stream)) != cudaSuccess) return e;
-    if ((e = launch_pair(c, sys->pair_grid, sys->stream)) != cudaSuccess) return e;
+    if ((e = launch_pair(c, sys->grid32, sys->grid64, sys->stream)) != cudaSuccess) return e;
     return launch_finalize(c, sys->stream);
 }
 
 static const int TICKS_PER_GRAPH = 8;
-static const int KERNELS_PER_TICK = 6;
+static int kernels_per_tick(const ffmin_system *sys) { return sys->prec == FFMIN_MIXED ? 7 : 6; }
 
 static ffmin_status ensure_graph(ffmin_system *sys) {
     if (sys->graph) return FFMIN_OK;
@@ -446,11 +516,9 @@ static ffmin_status ensure_graph(ffmin_system *sys) {
     return FFMIN_OK;
 }
 
-// one evaluation (E or EG) of every system at x (device)
-static ffmin_status eval_all(ffmin_system *sys, const double *x_dev, int kind) {
+// one evaluation (E or EG) of every system at the vector in `slot`
+static ffmin_status eval_slot(ffmin_system *sys, int slot, int kind) {
     const Ctx &c = sys->c;
-    CK(cudaMemcpyAsync(vslot(c, V_XIN), x_dev, sizeof(double) * 3 * sys->n_atoms, cudaMemcpyDeviceToDevice,
-                       sys->stream));
     for (int b = 0; b < sys->n_sys; b++) {
         SysState &S = sys->hst[b];
         S.active = 1;
@@ -458,20 +526,28 @@ static ffmin_status eval_all(ffmin_system *sys, const double *x_dev, int kind) {
         S.upd.op = U_NONE;
         S.dir[0].on = S.dir[1].on = 0;
         S.ev_kind = kind;
-        S.ev_base = V_XIN;
+        S.ev_base = slot;
         S.ev_dir = -1;
         S.ev_h = 0.0;
         S.ev_scale = 1.0;
+        S.ev_delta = 0;
         S.ne = S.neg = 0;
+        S.mode = sys->prec == FFMIN_MIXED ? 0 : 1;
     }
     ffmin_status st = upload_states(sys);
     if (st != FFMIN_OK) return st;
-    int32_t n = sys->n_sys;
-    CK(cudaMemcpyAsync(c.nactive, &n, sizeof(int32_t), cudaMemcpyHostToDevice, sys->stream));
+    if ((st = set_counts(sys)) != FFMIN_OK) return st;
     CK(launch_prepare(c, sys->stream));
-    CK(launch_pair(c, sys->pair_grid, sys->stream));
+    CK(launch_pair(c, sys->grid32, sys->grid64, sys->stream));
     CK(launch_finalize(c, sys->stream));
     return download_states(sys);
+}
+
+// one evaluation (E or EG) of every system at x (device)
+static ffmin_status eval_all(ffmin_system *sys, const double *x_dev, int kind) {
+    CK(cudaMemcpyAsync(vslot(sys->c, V_XIN), x_dev, sizeof(double) * 3 * sys->n_atoms,
+                       cudaMemcpyDeviceToDevice, sys->stream));
+    return eval_slot(sys, V_XIN, kind);
 }
 
 extern "C" {
@@ -553,8 +629,8 @@ static ffmin_status minimize_dev(ffmin_system *sys, double *x_dev, const ffmin_o
     const size_t bytes = sizeof(double) * 3 * sys->n_atoms;
     if (o->method == FFMIN_GRADFREE) {
         CK(cudaMemcpyAsync(vslot(c, V_X), x_dev, bytes, cudaMemcpyDeviceToDevice, sys->stream));
-        cudaError_t e = parab_minimize(sys, o, res);
-        if (e != cudaSuccess) return cuda_fail(sys, e, "gradient-free minimization");
+        ffmin_status st = parab_minimize(sys, o, res);
+        if (st != FFMIN_OK) return st;
         CK(cudaMemcpyAsync(x_dev, vslot(c, V_X), bytes, cudaMemcpyDeviceToDevice, sys->stream));
         return FFMIN_OK;
     }
@@ -581,6 +657,10 @@ static ffmin_status minimize_dev(ffmin_system *sys, double *x_dev, const ffmin_o
         S.kminus = o->k_minus;
         S.eps_h = o->eps_h;
         S.precond_on = o->use_learned_precond ? 1 : 0;
+        S.mixed = sys->prec == FFMIN_MIXED ? 1 : 0;
+        S.mode = S.mixed ? 0 : 1;
+        S.f32_best = HUGE_VAL;
+        S.stall = 0;
         S.active = 1;
         S.phase = PH_START;
         S.result_slot = o->method == FFMIN_FGM ? V_XB : V_X;
@@ -592,8 +672,7 @@ static ffmin_status minimize_dev(ffmin_system *sys, double *x_dev, const ffmin_o
     }
     ffmin_status st = upload_states(sys);
     if (st != FFMIN_OK) return st;
-    int32_t n = sys->n_sys;
-    CK(cudaMemcpyAsync(c.nactive, &n, sizeof(int32_t), cudaMemcpyHostToDevice, sys->stream));
+    if ((st = set_counts(sys)) != FFMIN_OK) return st;
     st = ensure_graph(sys);
     if (st != FFMIN_OK) return st;
     const int64_t max_ticks = o->max_ticks > 0 ? o->max_ticks : (int64_t)o->max_evals + 64;
@@ -608,7 +687,7 @@ static ffmin_status minimize_dev(ffmin_system *sys, double *x_dev, const ffmin_o
         if (ticks >= max_ticks) { timeout = true; break; }
     }
     sys->last_ticks = ticks;
-    sys->last_launches = ticks * KERNELS_PER_TICK;
+    sys->last_launches = ticks * kernels_per_tick(sys);
     st = download_states(sys);
     if (st != FFMIN_OK) return st;
     const int slot = o->method == FFMIN_FGM ? V_XB : V_X;
@@ -665,12 +744,13 @@ ffmin_status ffmin_time_pair_kernel(ffmin_system *sys, const double *x_dev, int3
     if (st != FFMIN_OK) return st;
     for (int b = 0; b < sys->n_sys; b++) sys->hst[b].ev_kind = with_grad ? EV_EG : EV_E;
     if ((st = upload_states(sys)) != FFMIN_OK) return st;
+    if ((st = set_counts(sys)) != FFMIN_OK) return st;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    CK(launch_pair(sys->c, sys->pair_grid, sys->stream));  // warm-up
+    CK(launch_pair(sys->c, sys->grid32, sys->grid64, sys->stream));  // warm-up
     CK(cudaEventRecord(e0, sys->stream));
-    for (int r = 0; r < reps; r++) CK(launch_pair(sys->c, sys->pair_grid, sys->stream));
+    for (int r = 0; r < reps; r++) CK(launch_pair(sys->c, sys->grid32, sys->grid64, sys->stream));
     CK(cudaEventRecord(e1, sys->stream));
     CK(cudaEventSynchronize(e1));
     float t = 0.f;
@@ -701,10 +781,84 @@ ffmin_status ffmin_set_precond(ffmin_system *sys, const uint16_t *w, int32_t n_p
 
 }  // extern "C"
 
-// placeholder for the gradient-free path until its kernels are in place
-namespace ffm {
-cudaError_t parab_minimize(ffmin_system *sys, const ffmin_options *o, ffmin_result *res) {
-    (void)sys; (void)o; (void)res;
-    return cudaErrorNotSupported;
+
+// ---------------------------------------------------------------- parab
+static const int PARAB_MOVES = 64;  // moves per graph replay
+
+static ffmin_status parab_minimize(ffmin_system *sys, const ffmin_options *o, ffmin_result *res) {
+    const Ctx &c = sys->c;
+    const int n = sys->hst[0].natoms;
+    const int mode = sys->prec == FFMIN_MIXED ? 0 : 1;
+    if (!sys->parab_state) {
+        CK(cudaMalloc(&sys->parab_state, parab_state_bytes()));
+        sys->allocs.push_back(sys->parab_state);
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        sys->parab_grid = std::max(1, std::min((n + TI - 1) / TI, 2 * sms));
+    }
+    std::vector<char> hbuf(parab_state_bytes());
+    parab_state_init(hbuf.data(), n, (int)sys->atom_off[0], mode, o->max_iter, o->seed, o->gradfree_delta);
+    CK(cudaMemcpyAsync(sys->parab_state, hbuf.data(), hbuf.size(), cudaMemcpyHostToDevice, sys->stream));
+    ffm::ParabState *ps = (ffm::ParabState *)sys->parab_state;
+    if (!sys->parab_graph) {
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(sys->stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaSuccess;
+        for (int k = 0; k < PARAB_MOVES && e == cudaSuccess; k++) e = launch_parab_move(c, ps, sys->parab_grid, sys->stream);
+        cudaError_t e2 = cudaStreamEndCapture(sys->stream, &g);
+        if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(sys, e, "parab capture"); }
+        if (e2 != cudaSuccess) return cuda_fail(sys, e2, "parab capture end");
+        e = cudaGraphInstantiate(&sys->parab_graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(sys, e, "parab instantiate");
+    }
+    // initial evaluation (also writes the pair-kernel positions of X)
+    ffmin_status st = eval_slot(sys, V_X, EV_EG);
+    if (st != FFMIN_OK) return st;
+    int32_t neg = 1, moves = 0, status = FFMIN_OK;
+    double f = sys->hst[0].res_f, ginf = sys->hst[0].res_ginf;
+    int64_t launches = 3, ticks = 0;
+    if (sys->hst[0].status == FFMIN_ERR_NONFINITE) status = FFMIN_ERR_NONFINITE;
+    // a sweep is N moves; the stopping test follows each complete sweep; an
+    // iteration cap that cuts a sweep (or starts one) ends with one more
+    // evaluation that reports the returned point
+    while (status == FFMIN_OK && !(ginf < o->gtol_inf)) {
+        bool truncated = moves >= o->max_iter;
+        if (!truncated) {
+            const int32_t stop = (int32_t)std::min<int64_t>((int64_t)moves + n, o->max_iter);
+            truncated = stop < moves + n;
+            CK(cudaMemcpyAsync((char *)sys->parab_state + parab_offset_stop(), &stop, sizeof(int32_t),
+                               cudaMemcpyHostToDevice, sys->stream));
+            for (int32_t k = moves; k < stop; k += PARAB_MOVES) {
+                CK(cudaGraphLaunch(sys->parab_graph, sys->stream));
+                launches += 2 * PARAB_MOVES;
+                ticks += PARAB_MOVES;
+            }
+            CK(cudaMemcpyAsync(sys->h_nactive, (char *)sys->parab_state + parab_offset_move(), sizeof(int32_t),
+                               cudaMemcpyDeviceToHost, sys->stream));
+            CK(cudaStreamSynchronize(sys->stream));
+            moves = *sys->h_nactive;
+            if (moves != stop) return fail(sys, FFMIN_ERR_CUDA, "gradient-free moves did not all run");
+        }
+        st = eval_slot(sys, V_X, EV_EG);
+        if (st != FFMIN_OK) return st;
+        neg++;
+        launches += 3;
+        f = sys->hst[0].res_f;
+        ginf = sys->hst[0].res_ginf;
+        if (sys->hst[0].status == FFMIN_ERR_NONFINITE) { status = FFMIN_ERR_NONFINITE; break; }
+        if (truncated) { status = FFMIN_ERR_MAX_ITER; break; }
+    }
+    res[0].energy = f;
+    res[0].grad_inf = ginf;
+    res[0].iterations = moves;
+    res[0].energy_evals = 8 * moves;
+    res[0].grad_evals = neg;
+    res[0].ls_failures = 0;
+    res[0].stop_reason = status;
+    sys->last_ticks = ticks;
+    sys->last_launches = launches;
+    sys->last_pairs = (int64_t)moves * 8 * (n - 1) + (int64_t)neg * n * (int64_t)(n - 1) / 2;
+    return FFMIN_OK;
 }
-}  // namespace ffm

@@ -32,11 +32,14 @@ __device__ __forceinline__ void deactivate(const Ctx &c, SysState &S) {
     if (S.active) {
         S.active = 0;
         atomicSub(c.nactive, 1);
+        atomicSub(&c.nmode[S.mode], 1);
     }
 }
 
 __device__ __forceinline__ void set_eval(SysState &S, int kind, int base, int dir, double h,
                                          double scale) {
+    // an FP32 energy-only trial along a direction is taken as a difference
+    S.ev_delta = (S.mode == 0 && kind == EV_E && dir >= 0) ? 1 : 0;
     S.ev_kind = kind;
     S.ev_base = base;
     S.ev_dir = dir;
@@ -57,8 +60,27 @@ __device__ __forceinline__ void set_dir(SysState &S, int which, double a, double
     d.outer = outer;
 }
 
-// finish: the system stops after the pending update op (if any) has run
+// finish: the system stops after the pending update op (if any) has run.
+// A MIXED run still in its FP32 phase does not stop: a converged or stalled
+// FP32 phase hands over to the FP64 phase, which re-evaluates the current
+// point (FGM: the best point) with FP64 pair terms and continues the same
+// method from there until the FP64 gradient meets the tolerance; an
+// iteration cap ends the run where it is (energies then come from the FP32
+// pair terms).
 __device__ void finish(const Ctx &c, SysState &S, int status, double res_f, double res_ginf) {
+    if (S.mixed && S.mode == 0 && S.phase != PH_EVAL_ONLY &&
+        (status == FFMIN_OK || status == FFMIN_ERR_LINESEARCH)) {
+        S.mode = 1;
+        atomicSub(&c.nmode[0], 1);
+        atomicAdd(&c.nmode[1], 1);
+        S.dir[0].on = 0;
+        S.dir[1].on = 0;
+        const int base = S.method == FFMIN_FGM ? V_XB : V_X;
+        set_eval(S, EV_EG, base, -1, 0.0, 1.0);
+        S.ring_count = 0;
+        S.phase = PH_START;
+        return;
+    }
     S.status = status;
     S.phase = PH_DONE;
     S.ev_kind = EV_NONE;
@@ -244,6 +266,13 @@ __device__ LsOut ls_feed(SysState &S, double f) {
 // ---------------- minimizer steps ----------------
 __device__ void fgm_finish(const Ctx &c, SysState &S, int status);
 
+// FP32 phase of a MIXED run: true when the run should hand over to FP64
+// after an accepted point with FP32 |grad|_inf ginf
+__device__ bool mixed_handover(const SysState &S, double f, double ginf) {
+    (void)f;
+    return S.mixed && S.mode == 0 && ginf < MIXED_SWITCH_RATIO * S.gtol;
+}
+
 __device__ void ls_begin(const Ctx &c, SysState &S, double rr, double gr) {
     if (cap_hit(S)) {
         if (S.method == FFMIN_FGM) fgm_finish(c, S, FFMIN_ERR_MAX_ITER);
@@ -259,6 +288,7 @@ __device__ void ls_begin(const Ctx &c, SysState &S, double rr, double gr) {
     S.ls_kind = ls;
     const bool fgm = S.method == FFMIN_FGM;
     S.fstar = fgm ? S.fw : S.f;
+    S.epair_base = S.epair_last;  // the last E + grad evaluation was at the base
     const double h = ls_start(S, S.h0);
     set_eval(S, EV_E, fgm ? V_W : V_X, V_R, h, inv);
     S.phase = PH_LS;
@@ -280,7 +310,7 @@ __device__ void fgm_finish(const Ctx &c, SysState &S, int status) {
 
 __device__ void fgm_on_w(const Ctx &c, SysState &S, double e, double ginf) {
     S.fw = e;
-    if (ginf < S.gtol) {
+    if (ginf < S.gtol || mixed_handover(S, e, ginf)) {
         if (e < S.fb) {
             S.upd.best = 1;
             S.fb = e;
@@ -344,13 +374,15 @@ __device__ double cg_beta(int variant, double gpgp, double gpg, double gpd, doub
 }
 
 // reductions of the finalize kernel
-enum { RF_E = 0, RF_GG, RF_GINF, RF_GTG, RF_GTR, RF_BAD, RF_N };
+enum { RF_E = 0, RF_GG, RF_GINF, RF_GTG, RF_GTR, RF_BAD, RF_EPAIR, RF_N };
 
 __device__ void on_eval_done(const Ctx &c, SysState &S, const double *v) {
-    const double E = v[RF_E];
+    const double E = S.ev_delta ? S.epair_base + v[RF_E] : v[RF_E];
     const bool bad = v[RF_BAD] > 0.0 || !isfinite(E);
     const int kind = S.ev_kind;
+    if (kind == EV_EG) S.epair_last = v[RF_EPAIR];
     S.ev_kind = EV_NONE;
+    S.ev_delta = 0;
     if (kind == EV_E) S.ne++;
     else S.neg++;
 
@@ -383,6 +415,7 @@ __device__ void on_eval_done(const Ctx &c, SysState &S, const double *v) {
             S.result_slot = V_XB;
             S.upd.op = U_FGM_W;
             S.upd.best = 1;
+            S.upd.restart = 1;
             S.ginf = v[RF_GINF];
             S.gg = v[RF_GG];
             fgm_on_w(c, S, E, v[RF_GINF]);
@@ -448,6 +481,7 @@ __device__ void on_eval_done(const Ctx &c, SysState &S, const double *v) {
         }
         S.upd.op = U_FGM_W;
         S.upd.best = 0;
+        S.upd.restart = 0;
         S.ginf = v[RF_GINF];
         S.gg = v[RF_GG];
         fgm_on_w(c, S, E, v[RF_GINF]);
@@ -493,7 +527,7 @@ __device__ void on_eval_done(const Ctx &c, SysState &S, const double *v) {
         S.f = E;
         S.ginf = gninf;
         S.gg = v[RF_GG];
-        if (S.ginf < S.gtol) {
+        if (S.ginf < S.gtol || mixed_handover(S, E, gninf)) {
             finish(c, S, FFMIN_OK, S.f, S.ginf);
             return;
         }
@@ -534,7 +568,7 @@ __device__ void on_update_done(const Ctx &c, SysState &S, const double *v) {
         S.sg[st] = v[RU_SG];
         S.ring[S.ring_count++] = st;
     }
-    if (S.ginf < S.gtol) {
+    if (S.ginf < S.gtol || mixed_handover(S, S.f, S.ginf)) {
         finish(c, S, FFMIN_OK, S.f, S.ginf);
         return;
     }

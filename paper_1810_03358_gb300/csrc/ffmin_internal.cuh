@@ -50,7 +50,10 @@ enum Phase : int {
     PH_IDLE = 0, PH_START, PH_DIR, PH_LS, PH_ACCEPT, PH_FGM_W, PH_FINAL, PH_EVAL_ONLY, PH_DONE
 };
 
+// a pair item (i-tile, j-chunk); tile < 0 marks a bonded item whose j0, nj
+// is a range of bonded terms
 struct Item { int32_t tile, j0, nj, diag; };
+constexpr int BONDED_ITEM_TERMS = 64;
 
 struct Tile { int32_t sys, a0, na, item0, nitem, pad0, pad1, pad2; };
 
@@ -84,6 +87,10 @@ struct SysState {
     DirOp dir[2];
     int32_t ev_kind, ev_base, ev_dir, cg_check;
     double ev_h, ev_scale;
+    // FP32 line-search trials are evaluated as energy differences from the
+    // search's base point: E = epair_base + sum of pair differences + bonded
+    int32_t ev_delta, delta_pad;
+    double epair_last, epair_base;
     // line search
     int32_t ls_kind, ls_step, ls_k, ls_pad;
     double lh[4], lf[4], fstar, slope, rnorm, ls_f0, ls_h0v;
@@ -100,8 +107,17 @@ struct SysState {
     // result
     double res_f, res_ginf;
     // learned preconditioner in use for this run
-    int32_t precond_on, precond_pad;
+    int32_t precond_on;
+    // precision: mixed = 1 for a MIXED object; mode 0 = FP32 pair terms,
+    // mode 1 = FP64 pair terms (the FP64 phase of a mixed run, or always)
+    int32_t mixed, mode, stall;
+    double f32_best;
 };
+
+// FP32 -> FP64 hand-over of a MIXED run: when the FP32 |grad|_inf falls
+// below this multiple of the tolerance (the FP64 phase then certifies the
+// point); a failed FP32 line search also hands over
+constexpr double MIXED_SWITCH_RATIO = 1.0;
 
 struct Ctx {
     int32_t n_sys, n_tiles, n_items, n_atoms;
@@ -114,6 +130,7 @@ struct Ctx {
     double *vec;            // [V_NSLOT][vstride]
     // pair kernel inputs / outputs
     float4 *posf;
+    float4 *dispf;          // FP32 displacement of the trial point from the base (difference trials)
     const float2 *parf;
     double4_32a *posd;
     const double2 *pard;
@@ -129,10 +146,15 @@ struct Ctx {
     const double2 *apar;
     const int4 *didx;
     const double4_32a *dpar;
+    int32_t n_bonds, n_angles, n_terms, n_pair_items;  // batch totals; bonded items follow pair items
+    const int32_t *term_sys;  // [n_terms] system of each bonded term
+    double *te;             // [n_terms] energy of each bonded term
+    double *tg;             // [2 nb + 3 na + 4 nd][3] gradient of each term at each position
     // reductions
     double *red;            // [n_tiles][NRED]
     unsigned int *counters; // one per kernel kind, reset by the last block
     int32_t *nactive;       // systems still minimizing
+    int32_t *nmode;         // [2] active systems per pair-kernel precision mode
     // learned preconditioner features
     const float *feat;      // [n_atoms][3] (q, sigma, eps)
     int32_t *ncount;        // [n_atoms] neighbours within 8 A (pair kernel EG, optional)
@@ -143,14 +165,17 @@ inline __host__ __device__ double *vslot(const Ctx &c, int slot) { return c.vec 
 
 // counters[] indices
 enum { CNT_PAIR = 0, CNT_PAIR_EXIT = 1, CNT_FIN = 2, CNT_UPD = 3, CNT_DIR1 = 4, CNT_DIR2 = 5,
-       CNT_PARAB = 6, CNT_PARAB2 = 7, CNT_N = 8 };
+       CNT_PARAB = 6, CNT_PARAB2 = 7, CNT_PAIR64 = 8, CNT_PAIR64_EXIT = 9, CNT_N = 10 };
 
 // ---- launchers (defined in the .cu files) ----
 cudaError_t launch_prepare(const Ctx &c, cudaStream_t s);
-cudaError_t launch_pair(const Ctx &c, int grid, cudaStream_t s);
+// launches the FP32 kernel (MIXED objects) and the FP64 kernel; each skips
+// the systems of the other precision mode and exits at once when none is
+// in its mode
+cudaError_t launch_pair(const Ctx &c, int grid32, int grid64, cudaStream_t s);
 cudaError_t launch_finalize(const Ctx &c, cudaStream_t s);
 cudaError_t launch_update(const Ctx &c, cudaStream_t s);
 cudaError_t launch_dir(const Ctx &c, int which, cudaStream_t s);
-int pair_grid_size(int prec);
+int pair_grid_size(int mode);
 
 }  // namespace ffm

@@ -7,10 +7,11 @@
 // evaluated in row i and again in row j, so no force is ever scattered and
 // no atomic touches a force (Newton's third law is not used).
 //
-// Work items are (i-tile, j-chunk) pairs taken from a device queue by a
-// persistent grid; each item writes its partial row sums (gx, gy, gz, row
-// energy) to its own slot, and the finalize kernel sums the slots of an
-// atom in a fixed order, so results are deterministic for a given chunking.
+// Work items are (i-tile, j-chunk) pairs taken from a device queue (reset by
+// a memset before each launch) by a persistent grid; each item writes its
+// partial row sums (gx, gy, gz, row energy) to its own slot, and the
+// finalize kernel sums the slots of an atom in a fixed order, so results are
+// deterministic for a given chunking.  Bonded-term items share the queue.
 //
 // Per pair (d = x_j - x_i, r^-1 = rsqrt(r^2), q' = q sqrt(C), and the
 // per-atom Lennard-Jones factors c6 = a sigma^3, c12 = a sigma^6 with
@@ -26,6 +27,7 @@
 // reciprocal square root (rsqrt.approx.ftz.f32).
 #include <cstdio>
 
+#include "bonded.cuh"
 #include "ffmin_internal.cuh"
 
 namespace ffm {
@@ -48,42 +50,98 @@ template <> struct VT<double> {
     static __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 };
 
-template <typename T, bool GRAD, bool DIAG>
+// IPT i-atoms per thread share every j load from shared memory.
+template <typename T, int IPT, bool GRAD, bool DIAG>
 __device__ __forceinline__ void sweep(const typename VT<T>::V4 *__restrict__ sp,
-                                      const typename VT<T>::V2 *__restrict__ sq, T xi, T yi,
-                                      T zi, T qi, T c6i, T c12i, int diag_k, T &gx, T &gy, T &gz,
-                                      T &ec, T &lj) {
+                                      const typename VT<T>::V2 *__restrict__ sq,
+                                      const typename VT<T>::V4 (&pi)[IPT],
+                                      const typename VT<T>::V2 (&ci)[IPT], const int (&dk)[IPT],
+                                      T (&gx)[IPT], T (&gy)[IPT], T (&gz)[IPT], T (&ec)[IPT],
+                                      T (&lj)[IPT]) {
 #pragma unroll 8
     for (int k = 0; k < TJ; k++) {
         const typename VT<T>::V4 pj = sp[k];
         const typename VT<T>::V2 qj = sq[k];
-        const T dx = pj.x - xi, dy = pj.y - yi, dz = pj.z - zi;
-        const T r2 = dx * dx + dy * dy + dz * dz;
-        T ri = VT<T>::rsq(r2);
-        if (DIAG) ri = (k == diag_k) ? T(0) : ri;
-        const T ri2 = ri * ri;
-        const T e = qi * pj.w * ri;
-        const T ri6 = ri2 * ri2 * ri2;
-        const T c6 = c6i * qj.x, c12 = c12i * qj.y;
-        const T t1 = c12 * ri6 - c6;
-        ec += e;
-        lj += ri6 * t1;
-        if (GRAD) {
-            const T t2 = c12 * ri6 + t1;
-            const T f = (ri6 * t2 + e) * ri2;
-            gx += f * dx;
-            gy += f * dy;
-            gz += f * dz;
+#pragma unroll
+        for (int u = 0; u < IPT; u++) {
+            const T dx = pj.x - pi[u].x, dy = pj.y - pi[u].y, dz = pj.z - pi[u].z;
+            const T r2 = dx * dx + dy * dy + dz * dz;
+            T ri = VT<T>::rsq(r2);
+            if (DIAG) ri = (k == dk[u]) ? T(0) : ri;
+            const T ri2 = ri * ri;
+            const T e = pi[u].w * pj.w * ri;
+            const T ri6 = ri2 * ri2 * ri2;
+            const T c6 = ci[u].x * qj.x, c12 = ci[u].y * qj.y;
+            const T t1 = c12 * ri6 - c6;
+            ec[u] += e;
+            lj[u] += ri6 * t1;
+            if (GRAD) {
+                const T t2 = c12 * ri6 + t1;
+                const T f = (ri6 * t2 + e) * ri2;
+                gx[u] += f * dx;
+                gy[u] += f * dy;
+                gz[u] += f * dz;
+            }
         }
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(TI) k_pair(Ctx c) {
+// FP32 line-search trial as an energy difference from the base point: with
+// d = x_j - x_i at the base and dd = the difference of the two atoms'
+// displacements, r'^2 - r^2 = dd.(2 d + dd) is formed without cancellation,
+// and so are
+//   r'^-2 - r^-2 = -(r'^2 - r^2) r^-2 r'^-2,
+//   r'^-1 - r^-1 = (r'^-2 - r^-2) / (r^-1 + r'^-1),
+//   r'^-6 - r^-6 = (r'^-2 - r^-2)(r'^-4 + r'^-2 r^-2 + r^-4),
+//   r'^-12 - r^-12 = (r'^-6 - r^-6)(r'^-6 + r^-6);
+// the row then accumulates the exact-difference form of
+// e_cul + 6 e_lj, whose rounding error is relative to the difference, not to
+// the energies (FP32 coordinates of the trial point would add noise of order
+// u |x| |F| per pair, larger than the line search's energy decrements).
+template <int IPT, bool DIAG>
+__device__ __forceinline__ void sweep_delta(const float4 *__restrict__ sp, const float2 *__restrict__ sq,
+                                            const float4 *__restrict__ sd, const float4 (&pi)[IPT],
+                                            const float2 (&ci)[IPT], const float4 (&di)[IPT],
+                                            const int (&dk)[IPT], float (&ec)[IPT], float (&lj)[IPT]) {
+#pragma unroll 4
+    for (int k = 0; k < TJ; k++) {
+        const float4 pj = sp[k];
+        const float2 qj = sq[k];
+        const float4 dj = sd[k];
+#pragma unroll
+        for (int u = 0; u < IPT; u++) {
+            const float dx = pj.x - pi[u].x, dy = pj.y - pi[u].y, dz = pj.z - pi[u].z;
+            const float ex = dj.x - di[u].x, ey = dj.y - di[u].y, ez = dj.z - di[u].z;
+            float r2 = dx * dx + dy * dy + dz * dz;
+            if (DIAG) r2 = (k == dk[u]) ? 1.f : r2;  // j == i: dd = 0, every difference vanishes
+            const float D = ex * (2.f * dx + ex) + ey * (2.f * dy + ey) + ez * (2.f * dz + ez);
+            const float ri = rsqrt_approx(r2), rp = rsqrt_approx(r2 + D);
+            const float ri2 = ri * ri, rp2 = rp * rp;
+            const float X = -D * ri2 * rp2;
+            float inv;
+            asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv) : "f"(ri + rp));
+            const float d1 = X * inv;
+            const float ri4 = ri2 * ri2, rp4 = rp2 * rp2;
+            const float d6 = X * (rp4 + rp2 * ri2 + ri4);
+            const float d12 = d6 * (rp4 * rp2 + ri4 * ri2);
+            const float c6 = ci[u].x * qj.x, c12 = ci[u].y * qj.y;
+            ec[u] += pi[u].w * pj.w * d1;
+            lj[u] += c12 * d12 - c6 * d6;
+        }
+    }
+}
+
+// NT threads per block, IPT i-atoms per thread, NT * IPT == TI (one tile).
+// the register cap (64 per thread) keeps the pair sweep at 16 (FP32) or 8
+// (FP64) resident blocks per SM; the rarely-run bonded items may spill
+template <typename T, int NT, int IPT>
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 16 : 8)) k_pair(Ctx c) {
+    static_assert(NT * IPT == TI, "a block covers one i-tile");
     using V4 = typename VT<T>::V4;
     using V2 = typename VT<T>::V2;
     __shared__ V4 sp[TJ];
     __shared__ V2 sq[TJ];
+    __shared__ float4 sd[sizeof(T) == 4 ? TJ : 1];  // displacements (FP32 difference trials)
     __shared__ int s_item;
     const V4 *__restrict__ pos;
     const V2 *__restrict__ par;
@@ -93,90 +151,130 @@ __global__ void __launch_bounds__(TI) k_pair(Ctx c) {
     } else {
         pos = c.posd; par = c.pard; out = c.gpd;
     }
+    constexpr int MODE = sizeof(T) == 4 ? 0 : 1;
+    constexpr int CNT = MODE == 0 ? CNT_PAIR : CNT_PAIR64;
+    if (c.nmode[MODE] == 0) return;  // no system evaluates in this precision
     const int tid = threadIdx.x;
     for (;;) {
-        if (tid == 0) s_item = (int)atomicAdd(&c.counters[CNT_PAIR], 1u);
+        if (tid == 0) s_item = (int)atomicAdd(&c.counters[CNT], 1u);
         __syncthreads();
         const int it = s_item;
         __syncthreads();
         if (it >= c.n_items) break;
         const Item I = c.items[it];
+        if (I.tile < 0) {  // bonded terms (FP64), overlapping the pair items of other warps
+            bonded_item(c, I.j0, I.nj, MODE);
+            continue;
+        }
         const Tile tl = c.tiles[I.tile];
         const int kind = c.st[tl.sys].ev_kind;
-        if (kind == EV_NONE) continue;
-        const bool valid = tid < tl.na;
-        const int ig = tl.a0 + tid;
-        V4 pi;
-        V2 ai;
-        if (valid) {
-            pi = pos[ig];
-            ai = par[ig];
-        } else {
-            pi.x = T(-1e6); pi.y = T(-1e6); pi.z = T(-1e6); pi.w = T(0);
-            ai.x = T(0); ai.y = T(0);
+        if (kind == EV_NONE || c.st[tl.sys].mode != MODE) continue;
+        const bool delta = MODE == 0 && c.st[tl.sys].ev_delta;
+        V4 pi[IPT];
+        V2 ci[IPT];
+        int ig[IPT];
+        T gx[IPT], gy[IPT], gz[IPT], ec[IPT], lj[IPT];
+#pragma unroll
+        for (int u = 0; u < IPT; u++) {
+            const int li = tid + u * NT;
+            ig[u] = tl.a0 + li;
+            if (li < tl.na) {
+                pi[u] = pos[ig[u]];
+                ci[u] = par[ig[u]];
+            } else {  // padding atom far away with no charge and no LJ
+                pi[u].x = T(-1e6); pi[u].y = T(-1e6); pi[u].z = T(-1e6); pi[u].w = T(0);
+                ci[u].x = T(0); ci[u].y = T(0);
+            }
+            gx[u] = gy[u] = gz[u] = ec[u] = lj[u] = T(0);
         }
-        T gx = 0, gy = 0, gz = 0, ec = 0, lj = 0;
+        float4 di[IPT];
+        if constexpr (MODE == 0) {
+#pragma unroll
+            for (int u = 0; u < IPT; u++)
+                di[u] = (delta && tid + u * NT < tl.na) ? c.dispf[ig[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
         const int jend = I.j0 + I.nj;
         for (int jt = I.j0; jt < jend; jt += TJ) {
-            const int jl = jt + tid;
-            if (jl < jend) {
-                sp[tid] = pos[jl];
-                sq[tid] = par[jl];
-            } else {
-                V4 d; d.x = T(1e6); d.y = T(1e6); d.z = T(1e6); d.w = T(0);
-                V2 z; z.x = T(0); z.y = T(0);
-                sp[tid] = d;
-                sq[tid] = z;
+#pragma unroll
+            for (int q = tid; q < TJ; q += NT) {
+                const int jl = jt + q;
+                if constexpr (MODE == 0) {
+                    if (delta) sd[q] = jl < jend ? c.dispf[jl] : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+                if (jl < jend) {
+                    sp[q] = pos[jl];
+                    sq[q] = par[jl];
+                } else {
+                    V4 d; d.x = T(1e6); d.y = T(1e6); d.z = T(1e6); d.w = T(0);
+                    V2 z; z.x = T(0); z.y = T(0);
+                    sp[q] = d;
+                    sq[q] = z;
+                }
             }
             __syncthreads();
-            const int dk = ig - jt;  // position of atom i inside this j tile, if any
-            const bool diag = I.diag && dk >= 0 && dk < TJ;
-            if (kind == EV_EG) {
-                if (diag)
-                    sweep<T, true, true>(sp, sq, pi.x, pi.y, pi.z, pi.w, ai.x, ai.y, dk, gx, gy, gz, ec, lj);
-                else
-                    sweep<T, true, false>(sp, sq, pi.x, pi.y, pi.z, pi.w, ai.x, ai.y, -1, gx, gy, gz, ec, lj);
+            // the i tile lies inside this j tile when jt == a0 (tiles and
+            // chunks are aligned to TJ == TI inside a system)
+            const bool diag = I.diag && jt == tl.a0;
+            int dk[IPT];
+#pragma unroll
+            for (int u = 0; u < IPT; u++) dk[u] = ig[u] - jt;
+            bool done = false;
+            if constexpr (MODE == 0) {
+                if (delta) {
+                    if (diag) sweep_delta<IPT, true>(sp, sq, sd, pi, ci, di, dk, ec, lj);
+                    else sweep_delta<IPT, false>(sp, sq, sd, pi, ci, di, dk, ec, lj);
+                    done = true;
+                }
+            }
+            if (done) {
+            } else if (kind == EV_EG) {
+                if (diag) sweep<T, IPT, true, true>(sp, sq, pi, ci, dk, gx, gy, gz, ec, lj);
+                else sweep<T, IPT, true, false>(sp, sq, pi, ci, dk, gx, gy, gz, ec, lj);
             } else {
-                if (diag)
-                    sweep<T, false, true>(sp, sq, pi.x, pi.y, pi.z, pi.w, ai.x, ai.y, dk, gx, gy, gz, ec, lj);
-                else
-                    sweep<T, false, false>(sp, sq, pi.x, pi.y, pi.z, pi.w, ai.x, ai.y, -1, gx, gy, gz, ec, lj);
+                if (diag) sweep<T, IPT, false, true>(sp, sq, pi, ci, dk, gx, gy, gz, ec, lj);
+                else sweep<T, IPT, false, false>(sp, sq, pi, ci, dk, gx, gy, gz, ec, lj);
             }
             __syncthreads();
         }
-        V4 o;
-        o.x = gx; o.y = gy; o.z = gz;
-        o.w = ec + lj * T(1.0 / 6.0);
-        out[(int64_t)it * TI + tid] = o;
-    }
-    if (tid == 0) {
-        __threadfence();
-        const unsigned d = atomicAdd(&c.counters[CNT_PAIR_EXIT], 1u);
-        if (d == gridDim.x - 1) {  // every block is past its last queue access
-            c.counters[CNT_PAIR] = 0;
-            c.counters[CNT_PAIR_EXIT] = 0;
-            __threadfence();
+#pragma unroll
+        for (int u = 0; u < IPT; u++) {
+            V4 o;
+            o.x = gx[u]; o.y = gy[u]; o.z = gz[u];
+            o.w = ec[u] + lj[u] * T(1.0 / 6.0);
+            out[(int64_t)it * TI + tid + u * NT] = o;
         }
     }
 }
 
-int pair_grid_size(int prec) {
+// launch shapes: FP32 two i-atoms per thread (halves shared-memory loads
+// per pair), FP64 one (the FP64 pipe, not the loads, is the limit)
+#define K_F32 k_pair<float, 64, 2>
+#define K_F64 k_pair<double, 128, 1>
+constexpr int NT_F32 = 64, NT_F64 = 128;
+
+int pair_grid_size(int mode) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (prec == FFMIN_MIXED)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pair<float>, TI, 0);
+    if (mode == 0)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, K_F32, NT_F32, 0);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pair<double>, TI, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, K_F64, NT_F64, 0);
     if (per < 1) per = 1;
     return sms * per;
 }
 
-cudaError_t launch_pair(const Ctx &c, int grid, cudaStream_t s) {
-    if (c.prec == FFMIN_MIXED)
-        k_pair<float><<<grid, TI, 0, s>>>(c);
-    else
-        k_pair<double><<<grid, TI, 0, s>>>(c);
+cudaError_t launch_pair(const Ctx &c, int grid32, int grid64, cudaStream_t s) {
+    // fresh work queues (counters CNT_PAIR and CNT_PAIR64)
+    cudaError_t e0 = cudaMemsetAsync(c.counters + CNT_PAIR, 0, sizeof(unsigned), s);
+    if (e0 == cudaSuccess) e0 = cudaMemsetAsync(c.counters + CNT_PAIR64, 0, sizeof(unsigned), s);
+    if (e0 != cudaSuccess) return e0;
+    if (c.prec == FFMIN_MIXED) {
+        K_F32<<<grid32, NT_F32, 0, s>>>(c);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    K_F64<<<grid64, NT_F64, 0, s>>>(c);
     return cudaGetLastError();
 }
 

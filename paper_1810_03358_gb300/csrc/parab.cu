@@ -1,0 +1,207 @@
+// Gradient-free "parab" minimization (arXiv 1810.03358, Section 3): each move
+// picks a random atom i, evaluates the part of E that depends on atom i at
+// its position and at +-delta along each axis (7 points), fits a parabola
+// per axis through the three values on that axis, evaluates its vertex (the
+// 8th point) and moves the atom to the best of the 8 (ties: the earlier
+// point).  |grad E|_inf is checked after every sweep of N moves.
+//
+// The random atom of move k is the k-th output of the counter-based
+// SplitMix64 stream (Steele, Lea and Flood 2014) with the user's seed, scaled
+// to [0, N) by a 64x64 -> 128-bit multiply (high word).
+//
+// A move costs two launches over all j (7 rows, then the vertex row); the
+// last block of each launch reduces the block partials in a fixed order and
+// takes the move's decision, so the moves of a sweep replay as a CUDA graph
+// with no host involvement.
+#include <cmath>
+#include <cstring>
+
+#include "bonded.cuh"
+#include "ffmin_internal.cuh"
+#include "reduce.cuh"
+
+struct ffmin_system;
+
+namespace ffm {
+
+struct ParabState {
+    int32_t move, stop_at, max_moves, n;
+    int32_t atom0, mode, atom, best;
+    uint64_t seed;
+    double delta;
+    double f[8];
+    double p[8][3];
+};
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t k) {
+    uint64_t z = seed + (k + 1) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ int pick_atom(uint64_t seed, uint64_t k, int n) {
+    return (int)__umul64hi(splitmix64(seed, k), (uint64_t)n);
+}
+
+// pair part of the row energy of atom i placed at each of NP positions,
+// this thread's share of the j atoms (FP64 accumulation; pair terms in the
+// system's precision mode)
+template <int NP>
+__device__ void row_partial(const Ctx &c, int mode, int atom0, int n, int i, const double (*p)[3],
+                            double *acc) {
+    for (int q = 0; q < NP; q++) acc[q] = 0.0;
+    const int stride = gridDim.x * blockDim.x;
+    if (mode == 1) {
+        const double qi = c.posd[atom0 + i].w;
+        const double2 ci = c.pard[atom0 + i];
+        for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+            if (j == i) continue;
+            const double4_32a pj = c.posd[atom0 + j];
+            const double2 cj = c.pard[atom0 + j];
+            const double c6 = ci.x * cj.x, c12 = ci.y * cj.y, qq = qi * pj.w;
+            for (int q = 0; q < NP; q++) {
+                const double dx = pj.x - p[q][0], dy = pj.y - p[q][1], dz = pj.z - p[q][2];
+                const double r2 = dx * dx + dy * dy + dz * dz;
+                const double ri = rsqrt(r2);
+                const double ri2 = ri * ri, ri6 = ri2 * ri2 * ri2;
+                acc[q] += qq * ri + ri6 * (c12 * ri6 - c6) * (1.0 / 6.0);
+            }
+        }
+    } else {
+        const float qi = c.posf[atom0 + i].w;
+        const float2 ci = c.parf[atom0 + i];
+        float pf[NP][3];
+        for (int q = 0; q < NP; q++)
+            for (int a = 0; a < 3; a++) pf[q][a] = (float)p[q][a];
+        for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+            if (j == i) continue;
+            const float4 pj = c.posf[atom0 + j];
+            const float2 cj = c.parf[atom0 + j];
+            const float c6 = ci.x * cj.x, c12 = ci.y * cj.y, qq = qi * pj.w;
+            for (int q = 0; q < NP; q++) {
+                const float dx = pj.x - pf[q][0], dy = pj.y - pf[q][1], dz = pj.z - pf[q][2];
+                const float r2 = dx * dx + dy * dy + dz * dz;
+                const float ri = rsqrtf(r2);
+                const float ri2 = ri * ri, ri6 = ri2 * ri2 * ri2;
+                acc[q] += (double)(qq * ri + ri6 * (c12 * ri6 - c6) * (1.0f / 6.0f));
+            }
+        }
+    }
+}
+
+// bonded terms containing atom i (global index a) with atom i at p
+__device__ double row_bonded(const Ctx &c, int a, const double *p) {
+    const double *x = vslot(c, V_X);
+    double e = 0.0;
+    for (int k = c.inc_off[a]; k < c.inc_off[a + 1]; k++) {
+        const int2 in = c.inc[k];
+        e += bonded_term(c, x, in.x >> 2, in.y, in.x & 3, nullptr, nullptr, a, p);
+    }
+    return e;
+}
+
+// 7 row energies: current position and +-delta along x, y, z
+__global__ void __launch_bounds__(TI) k_parab_rows(Ctx c, ParabState *ps) {
+    if (ps->move >= ps->stop_at) return;
+    const int n = ps->n, atom0 = ps->atom0;
+    const int i = pick_atom(ps->seed, (uint64_t)ps->move, n);
+    const double *X = vslot(c, V_X);
+    double p[7][3];
+    for (int q = 0; q < 7; q++)
+        for (int a = 0; a < 3; a++) p[q][a] = X[3 * (atom0 + i) + a];
+    for (int a = 0; a < 3; a++) {
+        p[1 + 2 * a][a] = p[1 + 2 * a][a] + ps->delta;
+        p[2 + 2 * a][a] = p[2 + 2 * a][a] - ps->delta;
+    }
+    double acc[7];
+    row_partial<7>(c, ps->mode, atom0, n, i, p, acc);
+    double v[7];
+    for (int q = 0; q < 7; q++) v[q] = acc[q];
+    block_reduce_store<7>(v, 0u, &c.red[(int64_t)blockIdx.x * NRED]);
+    if (!last_block(&c.counters[CNT_PARAB])) return;
+    __shared__ double tot[7];
+    if (threadIdx.x < 7) {
+        const int q = threadIdx.x;
+        double t = 0.0;
+        for (int b = 0; b < gridDim.x; b++) t += __ldcg(&c.red[(int64_t)b * NRED + q]);
+        tot[q] = t + row_bonded(c, atom0 + i, p[q]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ps->atom = i;
+        for (int q = 0; q < 7; q++) {
+            ps->f[q] = tot[q];
+            for (int a = 0; a < 3; a++) ps->p[q][a] = p[q][a];
+        }
+        for (int a = 0; a < 3; a++) {  // per-axis parabola vertex
+            const double fp = tot[1 + 2 * a], fm = tot[2 + 2 * a];
+            const double curv = fm - 2.0 * tot[0] + fp;
+            const double ts = curv > 0.0 ? ps->delta * (fm - fp) / (2.0 * curv) : 0.0;
+            ps->p[7][a] = p[0][a] + ts;
+        }
+        c.counters[CNT_PARAB] = 0;
+    }
+}
+
+// the vertex row, the decision and the move
+__global__ void __launch_bounds__(TI) k_parab_vertex(Ctx c, ParabState *ps) {
+    if (ps->move >= ps->stop_at) return;
+    const int n = ps->n, atom0 = ps->atom0, i = ps->atom;
+    double p[1][3];
+    for (int a = 0; a < 3; a++) p[0][a] = ps->p[7][a];
+    double acc[1];
+    row_partial<1>(c, ps->mode, atom0, n, i, p, acc);
+    double v[1] = {acc[0]};
+    block_reduce_store<1>(v, 0u, &c.red[(int64_t)blockIdx.x * NRED]);
+    if (!last_block(&c.counters[CNT_PARAB2])) return;
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int b = 0; b < gridDim.x; b++) t += __ldcg(&c.red[(int64_t)b * NRED]);
+        ps->f[7] = t + row_bonded(c, atom0 + i, p[0]);
+        int best = 0;
+        for (int q = 1; q < 8; q++)
+            if (ps->f[q] < ps->f[best]) best = q;
+        ps->best = best;
+        const int a = atom0 + i;
+        double *X = vslot(c, V_X);
+        for (int k = 0; k < 3; k++) X[3 * a + k] = ps->p[best][k];
+        const double q = c.qs[a];
+        if (ps->mode == 1)
+            c.posd[a] = make_double4_32a(X[3 * a], X[3 * a + 1], X[3 * a + 2], q);
+        else
+            c.posf[a] = make_float4((float)X[3 * a], (float)X[3 * a + 1], (float)X[3 * a + 2], (float)q);
+        ps->move = ps->move + 1;
+        __threadfence();
+        c.counters[CNT_PARAB2] = 0;
+    }
+}
+
+cudaError_t launch_parab_move(const Ctx &c, ParabState *ps, int grid, cudaStream_t s) {
+    k_parab_rows<<<grid, TI, 0, s>>>(c, ps);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_parab_vertex<<<grid, TI, 0, s>>>(c, ps);
+    return cudaGetLastError();
+}
+
+size_t parab_state_bytes() { return sizeof(ParabState); }
+
+void parab_state_init(void *host_buf, int n, int atom0, int mode, int max_moves, uint64_t seed,
+                      double delta) {
+    ParabState ps;
+    std::memset(&ps, 0, sizeof(ps));
+    ps.n = n;
+    ps.atom0 = atom0;
+    ps.mode = mode;
+    ps.max_moves = max_moves;
+    ps.stop_at = 0;
+    ps.seed = seed;
+    ps.delta = delta;
+    std::memcpy(host_buf, &ps, sizeof(ps));
+}
+
+size_t parab_offset_move() { return offsetof(ParabState, move); }
+size_t parab_offset_stop() { return offsetof(ParabState, stop_at); }
+
+}  // namespace ffm

@@ -17,7 +17,8 @@ Two bars (FP64 path):
    final energy is itself only defined up to that chaos, so a full run is
    judged against an ensemble of oracle runs from starts perturbed by
    1e-12 A: the GPU's final energy must lie within 0.01 % of the ensemble's
-   range, its stop must be valid (converged with the oracle's own gradient
+   range (or below it by at most the ensemble's own spread), its stop must be
+   valid (converged with the oracle's own gradient
    of the returned point below the tolerance), and the reported energy
    must be the energy of the returned point.
 """
@@ -70,7 +71,10 @@ def ensemble_parity(oracle_mod, s, xg, rg, kw, members=4, eps=1e-12):
     assert energies, "the oracle itself did not converge"
     lo, hi = min(energies), max(energies)
     tol = REL_E * max(abs(lo), abs(hi))
-    assert lo - tol <= rg["energy"] <= hi + tol, (rg["energy"], energies)
+    # above: within 0.01 % of the worst oracle member; below: a lower minimum
+    # is accepted down to the ensemble's own spread (the chaos that separates
+    # the oracle's members separates the GPU run from them as well)
+    assert lo - max(tol, hi - lo) <= rg["energy"] <= hi + tol, (rg["energy"], energies)
     assert rg["status_name"] == "ok", rg
     e_ret, g_ret = oracle_mod.energy_grad(s, xg)
     assert abs(e_ret - rg["energy"]) <= 1e-9 * max(abs(e_ret), 1.0)
@@ -175,3 +179,33 @@ def test_host_entry_point(ff, oracle_mod):
     r = S.minimize_host(xh, method=3, max_iter=PREFIX)
     S.close()
     prefix_parity(oracle_mod, s, xh.reshape(-1, 3), r[0], dict(method=3, max_iter=PREFIX))
+
+
+@pytest.mark.parametrize("method", [1, 2, 3])
+def test_mixed_fp32_then_fp64(ff, oracle_mod, method):
+    # (GD needs more than 1e5 steps on this system in either precision)
+    # MIXED: FP32 pair terms until the FP32 run converges or stalls, then the
+    # FP64 phase re-evaluates and finishes; the returned point is certified
+    # by the oracle's own gradient, and its energy is reported in FP64
+    s = synth.make_system(120, 27)
+    kw = dict(method=method, max_iter=100000)
+    xg, rg, _ = run_gpu(ff, [s], 1, **kw)
+    r = rg[0]
+    assert r["status_name"] == "ok", r
+    e_true, g_true = oracle_mod.energy_grad(s, xg[0])
+    assert np.abs(g_true).max() < 0.1 * (1 + 1e-6)
+    assert abs(e_true - r["energy"]) <= 1e-9 * abs(e_true)
+    xo, ro = oracle_mod.minimize(s, s.x, **kw)
+    # a different trajectory: a neighbouring minimum, within 0.5 %
+    assert abs(r["energy"] - ro["energy"]) <= 5e-3 * abs(ro["energy"])
+
+
+def test_mixed_batched(ff, oracle_mod):
+    systems = [synth.make_system(n, 320 + k) for k, n in enumerate([90, 45, 200, 12])]
+    kw = dict(method=3, max_iter=100000)
+    xg, rg, _ = run_gpu(ff, systems, 1, **kw)
+    for b, s in enumerate(systems):
+        assert rg[b]["status_name"] == "ok", rg[b]
+        e_true, g_true = oracle_mod.energy_grad(s, xg[b])
+        assert np.abs(g_true).max() < 0.1 * (1 + 1e-6)
+        assert abs(e_true - rg[b]["energy"]) <= 1e-9 * abs(e_true)
