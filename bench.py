@@ -203,6 +203,8 @@ def bench_gpu(args):
     S32.close()
     value32 = sum(ev32) * pairs_per_eval * ws / sum(t32)
 
+    minim = {} if args.no_minimize else minimizations(args, ffmin, synth, torch, dev)
+
     peaks = load_peaks()
     achieved_fp64 = FLOPS_PER_PAIR_EG * pairs_per_eval / (ms_pair / 1e3) / 1e12
     achieved_fp32 = FLOPS_PER_PAIR_EG * pairs_per_eval / (ms_pair32 / 1e3) / 1e12
@@ -241,6 +243,7 @@ def bench_gpu(args):
                   "frac_of_fp32_peak": achieved_fp32 / fp32_peak,
                   "final_energy": r32["energy"], "final_energy_fp64": r64["energy"]},
         "pair_kernel_e_only_ms": ms_pair_e,
+        "minimize": minim,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
@@ -249,6 +252,49 @@ def bench_gpu(args):
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def minimizations(args, ffmin, synth, torch, dev):
+    """Minimizations per second to |grad E|_inf < 0.1 (L-BFGS m = 10): the
+    256-system batch (atom counts log-uniform in [200, 5000], seeds 1000 + b)
+    in MIXED precision, a 4-system sample of it in both precisions (like for
+    like, the FP64 batch would take minutes), and the paper-scale 3,334-atom
+    system in both precisions.  Each run is timed once with CUDA events."""
+    import numpy as np
+
+    def run(systems, prec):
+        S = ffmin.System(systems, prec)
+        x = torch.tensor(np.concatenate([q.x.reshape(-1) for q in systems]), dtype=torch.float64, device=dev)
+        S.minimize(x.clone(), method="LBFGS", max_iter=2)  # warm-up (graph capture)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        r = S.minimize(x, method="LBFGS", lbfgs_m=10, gtol_inf=0.1, max_iter=100000)
+        ev1.record()
+        torch.cuda.synchronize()
+        st = S.last_stats()
+        S.close()
+        t = ev0.elapsed_time(ev1) / 1e3
+        ok = sum(1 for q in r if q["status_name"] == "ok")
+        return {"n_sys": len(systems), "converged": ok, "seconds": t, "minimizations_per_s": ok / t,
+                "max_final_grad_inf": max(q["grad_inf"] for q in r),
+                "iterations_max": max(q["iterations"] for q in r),
+                "pair_interactions_per_s": st["pair_interactions"] / t, "gpu_launches": st["launches"]}
+
+    out = {}
+    batch = synth.make_batch(256)
+    out["batch256_mixed"] = run(batch, ffmin.FFMIN_MIXED)
+    sample = batch[:4]
+    out["sample4_fp64"] = run(sample, ffmin.FFMIN_FP64)
+    out["sample4_mixed"] = run(sample, ffmin.FFMIN_MIXED)
+    out["sample4_mixed_vs_plain_gpu"] = (out["sample4_mixed"]["minimizations_per_s"] /
+                                         max(out["sample4_fp64"]["minimizations_per_s"], 1e-30))
+    s3 = synth.make_system(3334, 2)
+    out["n3334_fp64"] = run([s3], ffmin.FFMIN_FP64)
+    out["n3334_mixed"] = run([s3], ffmin.FFMIN_MIXED)
+    out["n3334_mixed_vs_plain_gpu"] = (out["n3334_mixed"]["minimizations_per_s"] /
+                                       max(out["n3334_fp64"]["minimizations_per_s"], 1e-30))
+    return out
 
 
 def cpu_baseline():
@@ -352,6 +398,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ffmin")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-minimize", action="store_true", help="skip the minimizations/s runs")
     ap.add_argument("--profile", action="store_true", help="small fixed workload for ncu")
     ap.add_argument("--profile-atoms", type=int, default=N_ATOMS)
     ap.add_argument("--profile-minimize", type=int, default=0)

@@ -354,6 +354,7 @@ ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t pre
     c.n_atoms = (int)total;
     c.vstride = ((3 * total + 31) / 32) * 32;
     c.prec = precision;
+    c.sep_reduce = n_sys >= 8 ? 1 : 0;
 
 #define CKC(call)                                                              \
     do {                                                                       \
@@ -488,17 +489,25 @@ static ffmin_status set_counts(ffmin_system *sys) {
 
 static cudaError_t launch_tick(ffmin_system *sys) {
     const Ctx &c = sys->c;
+    cudaStream_t s = sys->stream;
     cudaError_t e;
-    if ((e = launch_update(c, sys->stream)) != cudaSuccess) return e;
-    if ((e = launch_dir(c, 0, sys->stream)) != cudaSuccess) return e;
-    if ((e = launch_dir(c, 1, sys->stream)) != cudaSuccess) return e;
-    if ((e = launch_prepare(c, sys->stream)) != cudaSuccess) return e;
-    if ((e = launch_pair(c, sys->grid32, sys->grid64, sys->stream)) != cudaSuccess) return e;
-    return launch_finalize(c, sys->stream);
+    if ((e = launch_update(c, s)) != cudaSuccess) return e;
+    if (c.sep_reduce && (e = launch_sysreduce(c, 0, s)) != cudaSuccess) return e;
+    if ((e = launch_dir(c, 0, s)) != cudaSuccess) return e;
+    if (c.sep_reduce && (e = launch_sysreduce(c, 1, s)) != cudaSuccess) return e;
+    if ((e = launch_dir(c, 1, s)) != cudaSuccess) return e;
+    if (c.sep_reduce && (e = launch_sysreduce(c, 2, s)) != cudaSuccess) return e;
+    if ((e = launch_prepare(c, s)) != cudaSuccess) return e;
+    if ((e = launch_pair(c, sys->grid32, sys->grid64, s)) != cudaSuccess) return e;
+    if ((e = launch_finalize(c, s)) != cudaSuccess) return e;
+    if (c.sep_reduce) return launch_sysreduce(c, 3, s);
+    return cudaSuccess;
 }
 
 static const int TICKS_PER_GRAPH = 8;
-static int kernels_per_tick(const ffmin_system *sys) { return sys->prec == FFMIN_MIXED ? 7 : 6; }
+static int kernels_per_tick(const ffmin_system *sys) {
+    return (sys->prec == FFMIN_MIXED ? 7 : 6) + (sys->c.sep_reduce ? 4 : 0);
+}
 
 static ffmin_status ensure_graph(ffmin_system *sys) {
     if (sys->graph) return FFMIN_OK;
@@ -540,6 +549,7 @@ static ffmin_status eval_slot(ffmin_system *sys, int slot, int kind) {
     CK(launch_prepare(c, sys->stream));
     CK(launch_pair(c, sys->grid32, sys->grid64, sys->stream));
     CK(launch_finalize(c, sys->stream));
+    if (c.sep_reduce) CK(launch_sysreduce(c, 3, sys->stream));
     return download_states(sys);
 }
 

@@ -123,7 +123,7 @@ struct Ctx {
     int32_t n_sys, n_tiles, n_items, n_atoms;
     int64_t vstride;
     int32_t prec;           // ffmin_precision
-    int32_t pad;
+    int32_t sep_reduce;     // 1: per-system reductions + control in separate kernels (large batches)
     const Tile *tiles;
     const Item *items;
     SysState *st;
@@ -176,6 +176,9 @@ cudaError_t launch_pair(const Ctx &c, int grid32, int grid64, cudaStream_t s);
 cudaError_t launch_finalize(const Ctx &c, cudaStream_t s);
 cudaError_t launch_update(const Ctx &c, cudaStream_t s);
 cudaError_t launch_dir(const Ctx &c, int which, cudaStream_t s);
+// per-system reduction + control step after a stage (only when sep_reduce):
+// stage 0 update, 1 / 2 direction passes, 3 finalize
+cudaError_t launch_sysreduce(const Ctx &c, int stage, cudaStream_t s);
 int pair_grid_size(int mode);
 
 }  // namespace ffm

@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(TI) k_finalize(Ctx c) {
     }
     const unsigned maxmask = (1u << RF_GINF) | (1u << RF_BAD);
     block_reduce_store<RF_N>(v, maxmask, &c.red[(int64_t)blockIdx.x * NRED]);
-    if (!last_block(&c.counters[CNT_FIN])) return;
+    if (c.sep_reduce || !last_block(&c.counters[CNT_FIN])) return;
     last_block_systems<RF_N>(
         c, RF_N, maxmask, [](const SysState &S) { return S.ev_kind != EV_NONE; },
         [&](SysState &S, const double *tot) { on_eval_done(c, S, tot); }, nullptr);
@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(TI) k_update(Ctx c) {
             break;
         }
     }
-    if (!last_block(&c.counters[CNT_UPD])) return;
+    if (c.sep_reduce || !last_block(&c.counters[CNT_UPD])) return;
     last_block_systems<RU_N>(
         c, RU_N, 0u, [](const SysState &S) { return S.upd.op != U_NONE; },
         [&](SysState &S, const double *tot) { on_update_done(c, S, tot); },
@@ -255,13 +255,57 @@ __global__ void __launch_bounds__(TI) k_dir(Ctx c) {
         }
     }
     if (on) block_reduce_store_many(v, d.dots == 2 ? d.nY : 2, &c.red[(int64_t)blockIdx.x * NRED]);
-    if (!last_block(&c.counters[WHICH == 0 ? CNT_DIR1 : CNT_DIR2])) return;
+    if (c.sep_reduce || !last_block(&c.counters[WHICH == 0 ? CNT_DIR1 : CNT_DIR2])) return;
     last_block_systems<NRING>(
         c, 2, 0u, [](const SysState &S) { return S.dir[WHICH].on != 0; },
         [&](SysState &S, const double *tot) { on_dir_done(c, S, WHICH, tot); },
         [](const SysState &S) { return S.dir[WHICH].dots == 2 ? S.dir[WHICH].nY : 2; });
     __syncthreads();
     if (threadIdx.x == 0) c.counters[WHICH == 0 ? CNT_DIR1 : CNT_DIR2] = 0;
+}
+
+// one block per system: the system's tile partials of every value are summed
+// by the block's warps in tile order, then thread 0 runs the control step
+template <int STAGE>
+__global__ void __launch_bounds__(TI) k_sysreduce(Ctx c) {
+    SysState &S = c.st[blockIdx.x];
+    int nv;
+    unsigned maxmask = 0u;
+    if (STAGE == 0) {
+        if (S.upd.op == U_NONE) return;
+        nv = S.upd.op == U_PUSH ? RU_N : 0;
+    } else if (STAGE == 1 || STAGE == 2) {
+        const DirOp &d = S.dir[STAGE - 1];
+        if (!d.on) return;
+        nv = d.dots == 2 ? d.nY : 2;
+    } else {
+        if (S.ev_kind == EV_NONE) return;
+        nv = RF_N;
+        maxmask = (1u << RF_GINF) | (1u << RF_BAD);
+    }
+    __shared__ double tot[NRED];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int k = w; k < nv; k += NW) {
+        const double x = warp_sys_sum(c, S, k, (maxmask >> k) & 1u);
+        if (lane == 0) tot[k] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (STAGE == 0) on_update_done(c, S, tot);
+        else if (STAGE == 1) on_dir_done(c, S, 0, tot);
+        else if (STAGE == 2) on_dir_done(c, S, 1, tot);
+        else on_eval_done(c, S, tot);
+    }
+}
+
+cudaError_t launch_sysreduce(const Ctx &c, int stage, cudaStream_t s) {
+    switch (stage) {
+    case 0: k_sysreduce<0><<<c.n_sys, TI, 0, s>>>(c); break;
+    case 1: k_sysreduce<1><<<c.n_sys, TI, 0, s>>>(c); break;
+    case 2: k_sysreduce<2><<<c.n_sys, TI, 0, s>>>(c); break;
+    default: k_sysreduce<3><<<c.n_sys, TI, 0, s>>>(c); break;
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_prepare(const Ctx &c, cudaStream_t s) {
