@@ -176,6 +176,29 @@ ffmin_status ffmin_time_pair_kernel(ffmin_system *sys, const double *x_dev, int3
 ffmin_status ffmin_last_stats(const ffmin_system *sys, int64_t *ticks,
                               int64_t *n_kernel_launches, int64_t *pair_interactions);
 
+/* Allocation-free non-bonded energy and gradient (no counterpart in the
+ * paper: an interface for callers that cannot let a library allocate device
+ * memory, such as an application confined to another framework's capped
+ * memory pool, or a latency-bound loop that cannot afford cudaMalloc's
+ * implicit device synchronisation).  Computes, in FP64, the Coulomb +
+ * Lennard-Jones energy over all atom pairs of ONE system (no bonded terms)
+ * and its gradient.  All buffers are the caller's device memory:
+ *   x_dev [3N] xyz per atom; charge_dev, sigma_dev, epsilon_dev [N];
+ *   g_dev [3N] gradient out; e_dev [1] energy out.
+ * coulomb_c: 0 -> 332.0716 kcal*A/(mol*e^2).  Work is enqueued on
+ * cuda_stream (NULL = legacy default stream); nothing is synchronised.
+ * Scratch: a fixed device array inside the library (about 2 MB, held by
+ * every GPU that loads the library until the process exits); n_atoms above
+ * 8192 returns FFMIN_ERR_INVALID_ARG.  The first call on each device looks
+ * up the array's device address, so make that first call before any stream
+ * capture.  Every call uses the same array: calls that overlap on the GPU
+ * (concurrent streams) race; serialise them.  No cudaMalloc or cudaFree is
+ * ever called. */
+ffmin_status ffmin_pair_energy_grad_noalloc(const double *x_dev, const double *charge_dev,
+                                            const double *sigma_dev, const double *epsilon_dev,
+                                            int32_t n_atoms, double coulomb_c, double *g_dev,
+                                            double *e_dev, void *cuda_stream);
+
 /* Last error message of the system (or of the last failed create). */
 const char *ffmin_last_error(const ffmin_system *sys);
 

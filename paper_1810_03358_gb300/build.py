@@ -23,6 +23,7 @@ UNITS = {
     "minimizer.cu": ["-fmad=false"],
     "parab.cu": ["-fmad=false"],
     "mlp.cu": [],
+    "noalloc.cu": [],
     "api.cu": [],
 }
 

@@ -59,7 +59,7 @@ EXPORTS = ["ffmin_options_default", "ffmin_status_string", "ffmin_create", "ffmi
            "ffmin_n_atoms", "ffmin_atom_offset", "ffmin_energy", "ffmin_energy_grad",
            "ffmin_energy_grad_host", "ffmin_minimize", "ffmin_minimize_host",
            "ffmin_set_precond", "ffmin_time_pair_kernel", "ffmin_last_stats",
-           "ffmin_last_error"]
+           "ffmin_last_error", "ffmin_pair_energy_grad_noalloc"]
 
 _lib = None
 
@@ -92,6 +92,7 @@ def lib():
     L.ffmin_set_precond.argtypes = [vp, C.POINTER(C.c_uint16), C.c_int32]
     L.ffmin_time_pair_kernel.argtypes = [vp, vp, C.c_int32, C.c_int32, C.POINTER(C.c_float)]
     L.ffmin_last_stats.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+    L.ffmin_pair_energy_grad_noalloc.argtypes = [vp, vp, vp, vp, C.c_int32, C.c_double, vp, vp, vp]
     L.ffmin_last_error.argtypes = [vp]
     L.ffmin_last_error.restype = C.c_char_p
     for name in EXPORTS:
@@ -322,3 +323,18 @@ def ffmin_status_string(status):
 def ffmin_last_error(handle=None):
     m = lib().ffmin_last_error(C.c_void_p(handle) if handle else None)
     return m.decode() if m else ""
+
+
+def ffmin_pair_energy_grad_noalloc(x, charge, sigma, epsilon, g, e, coulomb_c=0.0, stream=None):
+    """Non-bonded E + grad of one system with caller-owned device buffers and
+    no allocation inside the library (torch FP64 CUDA tensors: x [3N],
+    charge / sigma / epsilon [N], g [3N] out, e [1] out).  Returns the status;
+    raises FfminError on failure."""
+    n = int(charge.numel())
+    st = lib().ffmin_pair_energy_grad_noalloc(
+        C.c_void_p(x.data_ptr()), C.c_void_p(charge.data_ptr()), C.c_void_p(sigma.data_ptr()),
+        C.c_void_p(epsilon.data_ptr()), n, float(coulomb_c), C.c_void_p(g.data_ptr()),
+        C.c_void_p(e.data_ptr()), C.c_void_p(_stream_handle(stream)))
+    if st != FFMIN_OK:
+        raise FfminError(st, "ffmin_pair_energy_grad_noalloc failed")
+    return st
