@@ -257,19 +257,26 @@ def bench_gpu(args):
 def minimizations(args, ffmin, synth, torch, dev):
     """Minimizations per second to |grad E|_inf < 0.1 (L-BFGS m = 10): the
     256-system batch (atom counts log-uniform in [200, 5000], seeds 1000 + b)
-    in MIXED precision, a 4-system sample of it in both precisions (like for
-    like, the FP64 batch would take minutes), and the paper-scale 3,334-atom
-    system in both precisions.  Each run is timed once with CUDA events."""
+    in MIXED precision with and without the learned preconditioner (trained
+    on other seeds), a 4-system sample of it in FP64 and MIXED (like for like;
+    the FP64 batch would take many minutes), and the paper-scale 3,334-atom
+    system.  Each run is timed once with CUDA events."""
     import numpy as np
 
-    def run(systems, prec):
+    from paper_1810_03358_gb300 import learn
+    w16 = learn.load_weights()
+
+    def run(systems, prec, learned=False):
         S = ffmin.System(systems, prec)
+        if learned:
+            ffmin.ffmin_set_precond(S.handle, w16)
         x = torch.tensor(np.concatenate([q.x.reshape(-1) for q in systems]), dtype=torch.float64, device=dev)
-        S.minimize(x.clone(), method="LBFGS", max_iter=2)  # warm-up (graph capture)
+        S.minimize(x.clone(), method="LBFGS", max_iter=2, use_learned_precond=int(learned))  # warm-up
         torch.cuda.synchronize()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record()
-        r = S.minimize(x, method="LBFGS", lbfgs_m=10, gtol_inf=0.1, max_iter=100000)
+        r = S.minimize(x, method="LBFGS", lbfgs_m=10, gtol_inf=0.1, max_iter=100000,
+                       use_learned_precond=int(learned))
         ev1.record()
         torch.cuda.synchronize()
         st = S.last_stats()
@@ -279,21 +286,32 @@ def minimizations(args, ffmin, synth, torch, dev):
         return {"n_sys": len(systems), "converged": ok, "seconds": t, "minimizations_per_s": ok / t,
                 "max_final_grad_inf": max(q["grad_inf"] for q in r),
                 "iterations_max": max(q["iterations"] for q in r),
+                "iterations_sum": sum(q["iterations"] for q in r),
                 "pair_interactions_per_s": st["pair_interactions"] / t, "gpu_launches": st["launches"]}
 
-    out = {}
+    def ratio(a, b):
+        return out[a]["minimizations_per_s"] / max(out[b]["minimizations_per_s"], 1e-30)
+
+    out = {"learned_weights": "paper_1810_03358_gb300/precond_w16.npy" if w16 is not None else None}
     batch = synth.make_batch(256)
     out["batch256_mixed"] = run(batch, ffmin.FFMIN_MIXED)
+    if w16 is not None:
+        out["batch256_mixed_learned"] = run(batch, ffmin.FFMIN_MIXED, learned=True)
+        out["batch256_learned_vs_mixed"] = ratio("batch256_mixed_learned", "batch256_mixed")
     sample = batch[:4]
     out["sample4_fp64"] = run(sample, ffmin.FFMIN_FP64)
     out["sample4_mixed"] = run(sample, ffmin.FFMIN_MIXED)
-    out["sample4_mixed_vs_plain_gpu"] = (out["sample4_mixed"]["minimizations_per_s"] /
-                                         max(out["sample4_fp64"]["minimizations_per_s"], 1e-30))
+    out["sample4_mixed_vs_plain_gpu"] = ratio("sample4_mixed", "sample4_fp64")
+    if w16 is not None:
+        out["sample4_mixed_learned"] = run(sample, ffmin.FFMIN_MIXED, learned=True)
+        out["sample4_mixed_learned_vs_plain_gpu"] = ratio("sample4_mixed_learned", "sample4_fp64")
     s3 = synth.make_system(3334, 2)
     out["n3334_fp64"] = run([s3], ffmin.FFMIN_FP64)
     out["n3334_mixed"] = run([s3], ffmin.FFMIN_MIXED)
-    out["n3334_mixed_vs_plain_gpu"] = (out["n3334_mixed"]["minimizations_per_s"] /
-                                       max(out["n3334_fp64"]["minimizations_per_s"], 1e-30))
+    out["n3334_mixed_vs_plain_gpu"] = ratio("n3334_mixed", "n3334_fp64")
+    if w16 is not None:
+        out["n3334_mixed_learned"] = run([s3], ffmin.FFMIN_MIXED, learned=True)
+        out["n3334_mixed_learned_vs_plain_gpu"] = ratio("n3334_mixed_learned", "n3334_fp64")
     return out
 
 

@@ -98,6 +98,13 @@ typedef struct {
     uint64_t seed;           /* GRADFREE atom picker seed (SplitMix64 stream) */
     int32_t use_learned_precond; /* L-BFGS: scale H0 by the learned per-atom diagonal */
     int32_t max_ticks;       /* safety bound on device evaluation rounds; 0 -> max_evals + 64 */
+    /* L-BFGS trajectory recording (training data of the preconditioner):
+     * when record_dev != NULL, after every record_every-th accepted step k
+     * (slot k / record_every - 1 < record_slots) every atom i of every system
+     * writes (<s_i, y_i>, <y_i, y_i>, |grad_i| before the step, 1) to
+     * record_dev[(slot * total_atoms + i) * 4 + 0..3] (device, FP64). */
+    double *record_dev;
+    int32_t record_every, record_slots;
 } ffmin_options;
 
 typedef struct {
@@ -164,6 +171,27 @@ ffmin_status ffmin_minimize_host(ffmin_system *sys, double *x_host, const ffmin_
  * H0 = gamma * diag(exp(clamp(z_i, -3, 3))) over the atom's 3 coordinates.
  * The paper has no counterpart; this is an extension of Algorithm 3. */
 ffmin_status ffmin_set_precond(ffmin_system *sys, const uint16_t *w_fp16_host, int32_t n_params);
+
+/* Neighbour counts: counts_dev[i] = number of atoms j != i of i's system
+ * with |x_i - x_j| < 8 A at x_dev (device), a feature of the
+ * preconditioner network.  Not in the paper. */
+ffmin_status ffmin_neighbour_counts(ffmin_system *sys, const double *x_dev, int32_t *counts_dev);
+
+/* Train the preconditioner network on the GPU (hand-written forward,
+ * backward and Adam kernels, FP32): steps Adam steps (learning rate lr) on
+ * minibatches of `batch` rows drawn from n_samples rows of feat_dev
+ * [n][5] / target_dev [n] (device) with the SplitMix64 stream of `seed`;
+ * loss = mean (z - t)^2.  w32_dev [449] FP32 weights (in/out), adam_dev
+ * [898] moment estimates (in/out, zero at the start), work_dev
+ * [ffmin_mlp_work_floats()] scratch, loss_host [steps] (optional) the
+ * minibatch losses, w16_dev [449] (optional) FP16 weights out.  steps = 0
+ * computes the mean-loss gradient over the first min(batch, n) rows into
+ * work_dev[work - 449 .. work) without updating.  Synchronizes the stream. */
+ffmin_status ffmin_mlp_train(const float *feat_dev, const float *target_dev, int64_t n_samples,
+                             int32_t steps, int32_t batch, float lr, uint64_t seed, float *w32_dev,
+                             float *adam_dev, float *work_dev, float *loss_host, uint16_t *w16_dev,
+                             void *cuda_stream);
+int64_t ffmin_mlp_work_floats(void);
 
 /* Time the dominant pair kernel alone: reps launches at x_dev with (1) or
  * without (0) forces, CUDA events on the system's stream; *ms = mean

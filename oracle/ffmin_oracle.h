@@ -96,6 +96,7 @@ typedef struct {
     double gradfree_delta;
     uint64_t seed;
     const double *precond_d;   /* optional fixed per-variable H0 diagonal [n] (L-BFGS) */
+    const double *mlp_w;       /* optional network [ORC_MLP_NW]: H0 diagonal per iteration (force field) */
 } orc_options;
 
 typedef struct {
@@ -120,6 +121,14 @@ int32_t orc_trace(double *f, double *h, double *theta, double *beta, int32_t cap
  * oldest first (s[k*n..], y[k*n..]); d is an optional H0 diagonal. */
 void orc_lbfgs_direction(int32_t n, const double *g, int32_t count, const double *s,
                          const double *y, const double *d, double *r);
+
+/* ---- preconditioner network (not in the paper) ---- */
+#define ORC_MLP_NW 449
+double orc_mlp_forward(const double *w, const double *f, double *h);
+double orc_mlp_loss_grad(const double *w, const double *feat, const double *target, int64_t n,
+                         double *grad);
+void orc_mlp_features(double q, double sigma, double eps, int32_t n8, double gnorm, double *f);
+void orc_precond_diag(const orc_ff *ff, const double *w, const int32_t *n8, const double *g, double *d);
 
 /* SplitMix64 (Steele, Lea, Flood 2014): the k-th output of the counter-based
  * stream with the given seed, and the atom it picks among n. */

@@ -317,6 +317,14 @@ static double cg_beta(int variant, int32_t n, const double *gp, const double *g,
 
 #define CAP_HIT(it, o) ((it) >= op->max_iter || (o).ne + (o).neg >= op->max_evals)
 
+/* optional per-iteration H0 diagonal of the force-field L-BFGS (the network) */
+typedef struct {
+    const orc_ff *ff;
+    const double *w;
+    int32_t *n8;
+} diag_ctx_t;
+static diag_ctx_t *g_diag = NULL;
+
 int orc_minimize(int32_t n, orc_fg_fn fg, void *ctx, double *x, const orc_options *op,
                  orc_result *res) {
     obj_t o = {n, fg, ctx, 0, 0, ORC_OK};
@@ -418,7 +426,12 @@ int orc_minimize(int32_t n, orc_fg_fn fg, void *ctx, double *x, const orc_option
     for (int32_t k = 0; k < n; k++) r[k] = -g[k];
     for (;;) {
         if (CAP_HIT(it, o)) { status = ORC_MAX_ITER; break; }
-        if (method == ORC_LBFGS)
+        if (method == ORC_LBFGS && g_diag && hist > 0) {
+            /* learned diagonal; plain L-BFGS when it gives no descent direction */
+            orc_precond_diag(g_diag->ff, g_diag->w, g_diag->n8, g, xt);
+            orc_lbfgs_direction(n, g, hist, S, Y, xt, r);
+            if (!(dotn(n, g, r) < 0.0)) orc_lbfgs_direction(n, g, hist, S, Y, NULL, r);
+        } else if (method == ORC_LBFGS)
             orc_lbfgs_direction(n, g, hist, S, Y, op->precond_d, r);
         else if (method == ORC_GD)
             for (int32_t k = 0; k < n; k++) r[k] = -g[k];
@@ -570,5 +583,19 @@ int orc_minimize_ff(const orc_ff *ff, double *x, const orc_options *o, orc_resul
     if (o->method == ORC_GRADFREE) return parab(ff, x, o, res);
     orc_options op = *o;
     if (op.cg_restart_every <= 0) op.cg_restart_every = 3 * ff->n_atoms;
-    return orc_minimize(3 * ff->n_atoms, ff_fg, (void *)ff, x, &op, res);
+    diag_ctx_t dc;
+    int32_t *n8 = NULL;
+    if (o->mlp_w && o->method == ORC_LBFGS) {
+        /* neighbour counts of the starting structure */
+        n8 = malloc(sizeof(int32_t) * (size_t)(ff->n_atoms > 0 ? ff->n_atoms : 1));
+        for (int i = 0; i < ff->n_atoms; i++) n8[i] = orc_neighbour_count(ff, x, i, 8.0);
+        dc.ff = ff;
+        dc.w = o->mlp_w;
+        dc.n8 = n8;
+        g_diag = &dc;
+    }
+    int st = orc_minimize(3 * ff->n_atoms, ff_fg, (void *)ff, x, &op, res);
+    g_diag = NULL;
+    free(n8);
+    return st;
 }

@@ -45,7 +45,8 @@ class _Opt(C.Structure):
                 ("max_evals", C.c_int32), ("cg_restart_every", C.c_int32), ("h0", C.c_double),
                 ("k_plus", C.c_double), ("k_minus", C.c_double), ("eps_h", C.c_double),
                 ("ls_par_K", C.c_int32), ("ls_par_g0", C.c_int32),
-                ("gradfree_delta", C.c_double), ("seed", C.c_uint64), ("precond_d", _dp)]
+                ("gradfree_delta", C.c_double), ("seed", C.c_uint64), ("precond_d", _dp),
+                ("mlp_w", _dp)]
 
 
 class _Res(C.Structure):
@@ -176,10 +177,12 @@ def options(**kw):
     o = _Opt()
     lib().orc_options_default(C.byref(o))
     keep = None
+    keep = []
     for k, v in kw.items():
-        if k == "precond_d":
-            keep = _f64(v) if v is not None else None
-            o.precond_d = _dptr(keep)
+        if k in ("precond_d", "mlp_w"):
+            arr = _f64(v) if v is not None else None
+            keep.append(arr)
+            setattr(o, k, _dptr(arr))
         else:
             setattr(o, k, v)
     return o, keep
@@ -277,5 +280,27 @@ def pick_atom(seed, k, n):
 
 
 def _bind_mlp(L):
-    L.orc_mlp_forward.argtypes = [C.c_int32, _dp, _dp, _dp, _dp, _dp, _dp]
-    L.orc_mlp_forward.restype = None
+    L.orc_mlp_forward.argtypes = [_dp, _dp, _dp]
+    L.orc_mlp_forward.restype = C.c_double
+    L.orc_mlp_loss_grad.argtypes = [_dp, _dp, _dp, C.c_int64, _dp]
+    L.orc_mlp_loss_grad.restype = C.c_double
+    L.orc_mlp_features.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int32, C.c_double, _dp]
+    L.orc_mlp_features.restype = None
+
+
+def mlp_forward(w, f):
+    w = _f64(w); f = _f64(f)
+    return lib().orc_mlp_forward(_dptr(w), _dptr(f), None)
+
+
+def mlp_loss_grad(w, feat, target):
+    w = _f64(w); feat = _f64(feat).reshape(-1, 5); target = _f64(target).reshape(-1)
+    g = np.zeros(449)
+    loss = lib().orc_mlp_loss_grad(_dptr(w), _dptr(feat), _dptr(target), target.size, _dptr(g))
+    return loss, g
+
+
+def mlp_features(q, sigma, eps, n8, gnorm):
+    f = np.zeros(5)
+    lib().orc_mlp_features(float(q), float(sigma), float(eps), int(n8), float(gnorm), _dptr(f))
+    return f

@@ -120,6 +120,9 @@ void ffmin_options_default(ffmin_options *o) {
     o->seed = 12345;
     o->use_learned_precond = 0;
     o->max_ticks = 0;
+    o->record_dev = nullptr;
+    o->record_every = 0;
+    o->record_slots = 0;
 }
 
 const char *ffmin_status_string(ffmin_status s) {
@@ -631,6 +634,8 @@ static ffmin_status check_options(ffmin_system *sys, const ffmin_options *o) {
         return fail(sys, FFMIN_ERR_INVALID_ARG, "GRADFREE needs one system and delta > 0");
     if (o->use_learned_precond && !sys->have_precond)
         return fail(sys, FFMIN_ERR_INVALID_ARG, "no preconditioner weights set");
+    if (o->record_dev && (o->record_every < 1 || o->record_slots < 1))
+        return fail(sys, FFMIN_ERR_INVALID_ARG, "recording needs record_every >= 1 and record_slots >= 1");
     return FFMIN_OK;
 }
 
@@ -647,6 +652,7 @@ static ffmin_status minimize_dev(ffmin_system *sys, double *x_dev, const ffmin_o
     CK(cudaMemcpyAsync(vslot(c, V_X), x_dev, bytes, cudaMemcpyDeviceToDevice, sys->stream));
     CK(cudaMemsetAsync(vslot(c, V_P), 0, bytes, sys->stream));
     CK(cudaMemsetAsync(vslot(c, V_R), 0, bytes, sys->stream));
+    if (o->use_learned_precond) CK(launch_ncount(c, vslot(c, V_X), c.ncount, sys->stream));
     for (int b = 0; b < sys->n_sys; b++) {
         SysState &S = sys->hst[b];
         const int32_t atom0 = S.atom0, natoms = S.natoms, tile0 = S.tile0, ntile = S.ntile;
@@ -666,7 +672,10 @@ static ffmin_status minimize_dev(ffmin_system *sys, double *x_dev, const ffmin_o
         S.kplus = o->k_plus;
         S.kminus = o->k_minus;
         S.eps_h = o->eps_h;
-        S.precond_on = o->use_learned_precond ? 1 : 0;
+        S.precond_on = (o->use_learned_precond && o->method == FFMIN_LBFGS) ? 1 : 0;
+        S.rec_ptr = o->record_dev;
+        S.rec_every = o->record_dev ? o->record_every : 0;
+        S.rec_slots = o->record_dev ? o->record_slots : 0;
         S.mixed = sys->prec == FFMIN_MIXED ? 1 : 0;
         S.mode = S.mixed ? 0 : 1;
         S.f32_best = HUGE_VAL;
@@ -770,6 +779,16 @@ ffmin_status ffmin_time_pair_kernel(ffmin_system *sys, const double *x_dev, int3
     *ms = t / (float)reps;
     for (int b = 0; b < sys->n_sys; b++) sys->hst[b].ev_kind = EV_NONE;
     if ((st = upload_states(sys)) != FFMIN_OK) return st;
+    return leave(sys);
+}
+
+ffmin_status ffmin_neighbour_counts(ffmin_system *sys, const double *x_dev, int32_t *counts_dev) {
+    ffmin_status st = enter(sys);
+    if (st != FFMIN_OK) return st;
+    if (!x_dev || !counts_dev) return fail(sys, FFMIN_ERR_INVALID_ARG, "NULL argument");
+    // the kernel reads each system's atom range from the device state
+    if ((st = upload_states(sys)) != FFMIN_OK) return st;
+    CK(launch_ncount(sys->c, x_dev, counts_dev, sys->stream));
     return leave(sys);
 }
 

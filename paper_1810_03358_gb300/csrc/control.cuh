@@ -273,7 +273,16 @@ __device__ bool mixed_handover(const SysState &S, double f, double ginf) {
     return S.mixed && S.mode == 0 && ginf < MIXED_SWITCH_RATIO * S.gtol;
 }
 
+__device__ void lbfgs_pass1(SysState &S, int use_d);
+
 __device__ void ls_begin(const Ctx &c, SysState &S, double rr, double gr) {
+    if (S.method == FFMIN_LBFGS && S.dir_used_d && !(gr < 0.0)) {
+        // the learned diagonal gave no descent direction: plain L-BFGS for
+        // this iteration (next round: both direction passes again)
+        lbfgs_pass1(S, 0);
+        return;
+    }
+    S.dir_used_d = 0;
     if (cap_hit(S)) {
         if (S.method == FFMIN_FGM) fgm_finish(c, S, FFMIN_ERR_MAX_ITER);
         else finish(c, S, FFMIN_ERR_MAX_ITER, S.f, S.ginf);
@@ -537,6 +546,24 @@ __device__ void on_eval_done(const Ctx &c, SysState &S, const double *v) {
     }
 }
 
+// first pass of the L-BFGS direction: r0 = gamma D (-g - sum alpha_j y_j)
+// with D the learned diagonal when use_d (else the identity)
+__device__ void lbfgs_pass1(SysState &S, int use_d) {
+    const int n = S.ring_count;
+    const int nw = S.ring[n - 1];
+    const double gamma = S.SY[nw][nw] / S.yy[nw];
+    DirOp &d = S.dir[0];
+    set_dir(S, 0, -1.0, 0.0, gamma, 2);
+    d.use_d = use_d;
+    S.dir_used_d = use_d;
+    d.nY = n;
+    for (int j = 0; j < n; j++) {  // newest first, as the vector recursion
+        const int a = S.ring[n - 1 - j];
+        d.sY[j] = a;
+        d.cY[j] = -S.alpha[a];
+    }
+}
+
 // reductions of the update kernel (U_PUSH)
 enum { RU_SY = 0, RU_YY, RU_SG, RU_SJY, RU_SJG = RU_SJY + NRING, RU_N = RU_SJG + NRING };
 
@@ -588,17 +615,7 @@ __device__ void on_update_done(const Ctx &c, SysState &S, const double *v) {
         }
         S.alpha[a] = S.rho[a] * q;
     }
-    const int nw = S.ring[n - 1];
-    const double gamma = S.SY[nw][nw] / S.yy[nw];
-    DirOp &d = S.dir[0];
-    set_dir(S, 0, -1.0, 0.0, gamma, 2);
-    d.use_d = S.precond_on;
-    d.nY = n;
-    for (int j = 0; j < n; j++) {  // newest first, as the vector recursion
-        const int a = S.ring[n - 1 - j];
-        d.sY[j] = a;
-        d.cY[j] = -S.alpha[a];
-    }
+    lbfgs_pass1(S, S.precond_on);
 }
 
 // reductions of the direction kernels

@@ -112,6 +112,10 @@ struct SysState {
     // mode 1 = FP64 pair terms (the FP64 phase of a mixed run, or always)
     int32_t mixed, mode, stall;
     double f32_best;
+    // preconditioner: 1 when the current direction used the learned diagonal
+    int32_t dir_used_d, rec_every;
+    int32_t rec_slots, rec_pad;
+    double *rec_ptr;
 };
 
 // FP32 -> FP64 hand-over of a MIXED run: when the FP32 |grad|_inf falls
@@ -169,6 +173,7 @@ enum { CNT_PAIR = 0, CNT_PAIR_EXIT = 1, CNT_FIN = 2, CNT_UPD = 3, CNT_DIR1 = 4, 
 
 // ---- launchers (defined in the .cu files) ----
 cudaError_t launch_prepare(const Ctx &c, cudaStream_t s);
+cudaError_t launch_ncount(const Ctx &c, const double *x, int32_t *out, cudaStream_t s);
 // launches the FP32 kernel (MIXED objects) and the FP64 kernel; each skips
 // the systems of the other precision mode and exits at once when none is
 // in its mode

@@ -21,6 +21,7 @@
 
 #include "bonded.cuh"
 #include "control.cuh"
+#include "mlp.cuh"
 #include "reduce.cuh"
 
 namespace ffm {
@@ -146,6 +147,16 @@ __global__ void __launch_bounds__(TI) k_update(Ctx c) {
             }
             v[RU_SY] = s[0] * y[0] + s[1] * y[1] + s[2] * y[2];
             v[RU_YY] = y[0] * y[0] + y[1] * y[1] + y[2] * y[2];
+            if (S.rec_ptr && S.rec_every > 0 && S.iter % S.rec_every == 0) {
+                const int slot = S.iter / S.rec_every - 1;
+                if (slot < S.rec_slots) {
+                    double *r = S.rec_ptr + ((int64_t)slot * c.n_atoms + t.a0 + i) * 4;
+                    r[0] = v[RU_SY];
+                    r[1] = v[RU_YY];
+                    r[2] = sqrt(G[0] * G[0] + G[1] * G[1] + G[2] * G[2]);
+                    r[3] = 1.0;
+                }
+            }
             v[RU_SG] = s[0] * GT[0] + s[1] * GT[1] + s[2] * GT[2];
             const int nS = S.upd.nS;
 #pragma unroll
@@ -215,11 +226,16 @@ __global__ void __launch_bounds__(TI) k_dir(Ctx c) {
 #pragma unroll
     for (int k = 0; k < NRING; k++) v[k] = 0.0;
     const bool on = d.on != 0;
+    __shared__ float w_mlp[MLP_NW];
+    if (on && d.use_d) {  // learned H0 diagonal: FP16 weights -> FP32 in shared memory
+        for (int k = threadIdx.x; k < MLP_NW; k += blockDim.x)
+            w_mlp[k] = __half2float(__ushort_as_half(c.mlp_w[k]));
+        __syncthreads();
+    }
     if (on && i < t.na) {
         const int64_t off = 3 * (int64_t)(t.a0 + i);
         const double *G = vslot(c, V_G) + off;
         double *R = vslot(c, V_R) + off;
-        const double *D = vslot(c, V_D) + off;
         double acc[3];
         for (int k = 0; k < 3; k++) {
             double x = 0.0;
@@ -237,8 +253,16 @@ __global__ void __launch_bounds__(TI) k_dir(Ctx c) {
             const double cs = d.cS[j];
             for (int k = 0; k < 3; k++) acc[k] = acc[k] + cs * s[k];
         }
+        double dscale = 1.0;
+        if (d.use_d) {
+            const int a = t.a0 + i;
+            float f[MLP_IN];
+            const double gn = sqrt(G[0] * G[0] + G[1] * G[1] + G[2] * G[2]);
+            mlp_features(c.feat[3 * a], c.feat[3 * a + 1], c.feat[3 * a + 2], c.ncount[a], (float)gn, f);
+            dscale = (double)mlp_scale(w_mlp, f);
+        }
         for (int k = 0; k < 3; k++) {
-            acc[k] = d.use_d ? (d.outer * D[k]) * acc[k] : d.outer * acc[k];
+            acc[k] = d.use_d ? (d.outer * dscale) * acc[k] : d.outer * acc[k];
             R[k] = acc[k];
         }
         if (d.dots == 1) {
@@ -305,6 +329,27 @@ cudaError_t launch_sysreduce(const Ctx &c, int stage, cudaStream_t s) {
     case 2: k_sysreduce<2><<<c.n_sys, TI, 0, s>>>(c); break;
     default: k_sysreduce<3><<<c.n_sys, TI, 0, s>>>(c); break;
     }
+    return cudaGetLastError();
+}
+
+// neighbours within 8 A of every atom inside its own system, from X
+__global__ void __launch_bounds__(TI) k_ncount(Ctx c, const double *x, int32_t *out) {
+    const Tile t = c.tiles[blockIdx.x];
+    const SysState &S = c.st[t.sys];
+    const int i = threadIdx.x;
+    if (i >= t.na) return;
+    const int a = t.a0 + i;
+    const float xi = (float)x[3 * a], yi = (float)x[3 * a + 1], zi = (float)x[3 * a + 2];
+    int n = 0;
+    for (int j = S.atom0; j < S.atom0 + S.natoms; j++) {
+        const float dx = (float)x[3 * j] - xi, dy = (float)x[3 * j + 1] - yi, dz = (float)x[3 * j + 2] - zi;
+        n += (j != a && dx * dx + dy * dy + dz * dz < 64.f) ? 1 : 0;
+    }
+    out[a] = n;
+}
+
+cudaError_t launch_ncount(const Ctx &c, const double *x, int32_t *out, cudaStream_t s) {
+    k_ncount<<<c.n_tiles, TI, 0, s>>>(c, x, out);
     return cudaGetLastError();
 }
 

@@ -46,7 +46,8 @@ class ffmin_options(C.Structure):
                 ("k_plus", C.c_double), ("k_minus", C.c_double), ("eps_h", C.c_double),
                 ("ls_par_K", C.c_int32), ("ls_par_g0", C.c_int32),
                 ("gradfree_delta", C.c_double), ("seed", C.c_uint64),
-                ("use_learned_precond", C.c_int32), ("max_ticks", C.c_int32)]
+                ("use_learned_precond", C.c_int32), ("max_ticks", C.c_int32),
+                ("record_dev", C.c_void_p), ("record_every", C.c_int32), ("record_slots", C.c_int32)]
 
 
 class ffmin_result(C.Structure):
@@ -59,7 +60,8 @@ EXPORTS = ["ffmin_options_default", "ffmin_status_string", "ffmin_create", "ffmi
            "ffmin_n_atoms", "ffmin_atom_offset", "ffmin_energy", "ffmin_energy_grad",
            "ffmin_energy_grad_host", "ffmin_minimize", "ffmin_minimize_host",
            "ffmin_set_precond", "ffmin_time_pair_kernel", "ffmin_last_stats",
-           "ffmin_last_error", "ffmin_pair_energy_grad_noalloc"]
+           "ffmin_last_error", "ffmin_pair_energy_grad_noalloc", "ffmin_neighbour_counts",
+           "ffmin_mlp_train", "ffmin_mlp_work_floats"]
 
 _lib = None
 
@@ -93,11 +95,16 @@ def lib():
     L.ffmin_time_pair_kernel.argtypes = [vp, vp, C.c_int32, C.c_int32, C.POINTER(C.c_float)]
     L.ffmin_last_stats.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
     L.ffmin_pair_energy_grad_noalloc.argtypes = [vp, vp, vp, vp, C.c_int32, C.c_double, vp, vp, vp]
+    L.ffmin_neighbour_counts.argtypes = [vp, vp, vp]
+    L.ffmin_mlp_train.argtypes = [vp, vp, C.c_int64, C.c_int32, C.c_int32, C.c_float, C.c_uint64, vp, vp,
+                                  vp, C.POINTER(C.c_float), vp, vp]
+    L.ffmin_mlp_work_floats.argtypes = []
+    L.ffmin_mlp_work_floats.restype = C.c_int64
     L.ffmin_last_error.argtypes = [vp]
     L.ffmin_last_error.restype = C.c_char_p
     for name in EXPORTS:
         if name not in ("ffmin_options_default", "ffmin_status_string", "ffmin_n_atoms",
-                        "ffmin_atom_offset", "ffmin_last_error"):
+                        "ffmin_atom_offset", "ffmin_last_error", "ffmin_mlp_work_floats"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -338,3 +345,32 @@ def ffmin_pair_energy_grad_noalloc(x, charge, sigma, epsilon, g, e, coulomb_c=0.
     if st != FFMIN_OK:
         raise FfminError(st, "ffmin_pair_energy_grad_noalloc failed")
     return st
+
+
+def ffmin_neighbour_counts(handle, x, counts):
+    """counts: int32 CUDA tensor [total atoms] (out)."""
+    st = lib().ffmin_neighbour_counts(C.c_void_p(handle), C.c_void_p(x.data_ptr()),
+                                      C.c_void_p(counts.data_ptr()))
+    _check(st, handle)
+
+
+def ffmin_mlp_work_floats():
+    return int(lib().ffmin_mlp_work_floats())
+
+
+def ffmin_mlp_train(feat, target, steps, batch, lr, seed, w32, adam, work, w16=None, stream=None):
+    """Adam steps of the preconditioner network on the GPU (float32 CUDA
+    tensors: feat [n, 5], target [n], w32 [449] in/out, adam [898] in/out,
+    work [ffmin_mlp_work_floats()]; w16 optional [449] uint16/int16 out).
+    Returns the per-step minibatch losses (numpy)."""
+    n = int(target.numel())
+    losses = np.zeros(max(steps, 1), dtype=np.float32)
+    st = lib().ffmin_mlp_train(
+        C.c_void_p(feat.data_ptr()), C.c_void_p(target.data_ptr()), n, int(steps), int(batch),
+        float(lr), int(seed), C.c_void_p(w32.data_ptr()),
+        C.c_void_p(adam.data_ptr()) if adam is not None else None, C.c_void_p(work.data_ptr()),
+        losses.ctypes.data_as(C.POINTER(C.c_float)),
+        C.c_void_p(w16.data_ptr()) if w16 is not None else None, C.c_void_p(_stream_handle(stream)))
+    if st != FFMIN_OK:
+        raise FfminError(st, "ffmin_mlp_train failed")
+    return losses

@@ -1,0 +1,76 @@
+"""The learned preconditioner on the GPU: training gradients of the
+hand-written kernels against the FP64 oracle, the identity network equal to
+plain L-BFGS, a trained network's preconditioned L-BFGS against the oracle
+over a capped prefix, and the end-to-end pipeline (record plain trajectories,
+train, minimize held-out systems with and without the network)."""
+import numpy as np
+import pytest
+
+from paper_1810_03358_gb300 import synth
+from tests.gpu_util import need_gpu, split, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ff():
+    return need_gpu()
+
+
+def test_training_gradient_matches_oracle(ff, oracle_mod):
+    from paper_1810_03358_gb300 import learn
+    rng = np.random.default_rng(5)
+    feat = np.stack([rng.uniform(-0.8, 0.8, 3000), rng.uniform(2.5, 3.8, 3000), rng.uniform(0.02, 0.2, 3000),
+                     rng.uniform(0, 2, 3000), rng.uniform(0, 8, 3000)], axis=1).astype(np.float32)
+    t = rng.normal(size=3000).astype(np.float32)
+    w = learn.init_weights(7)
+    w[320:] = rng.normal(scale=0.2, size=129)
+    g_gpu = learn.gradient(feat, t, w)
+    loss, g_orc = oracle_mod.mlp_loss_grad(w.astype(np.float64), feat.astype(np.float64), t.astype(np.float64))
+    assert np.abs(g_gpu - g_orc).max() <= 1e-4 * np.abs(g_orc).max() + 1e-6
+
+
+def test_identity_network_equals_plain(ff, oracle_mod):
+    s = synth.make_system(60, 42)
+    w16 = np.zeros(449, dtype=np.float16)
+    from paper_1810_03358_gb300 import learn
+    r0, _, x0 = learn.minimize_with([s], None, precision=0, use=False, max_iter=40)
+    r1, _, x1 = learn.minimize_with([s], w16, precision=0, use=True, max_iter=40)
+    assert r0[0]["iterations"] == r1[0]["iterations"] == 40
+    assert r0[0]["energy"] == r1[0]["energy"]
+    assert np.array_equal(x0.cpu().numpy(), x1.cpu().numpy())
+
+
+def test_preconditioned_prefix_matches_oracle(ff, oracle_mod):
+    from paper_1810_03358_gb300 import learn
+    s = synth.make_system(80, 43)
+    rng = np.random.default_rng(9)
+    w = learn.init_weights(9)
+    w[384:448] = rng.normal(scale=0.05, size=64)
+    w16 = w.astype(np.float16)
+    r, _, x = learn.minimize_with([s], w16, precision=0, use=True, max_iter=6)
+    xo, ro = oracle_mod.minimize(s, s.x, method=oracle_mod.LBFGS, max_iter=6,
+                                 mlp_w=w16.astype(np.float64))
+    assert r[0]["iterations"] == ro["iterations"] and r[0]["energy_evals"] == ro["energy_evals"]
+    # FP32 network arithmetic on the GPU vs FP64 in the oracle
+    assert abs(r[0]["energy"] - ro["energy"]) <= 1e-5 * abs(ro["energy"])
+
+
+def test_pipeline_train_and_gain(ff, oracle_mod):
+    from paper_1810_03358_gb300 import learn
+    train_sys = learn.training_systems(n_sys=12, seed0=20000, lo=300, hi=900)
+    feat, targ, _ = learn.record_trajectories(train_sys, record_every=10, record_slots=30)
+    assert len(targ) > 10000
+    w32, w16, losses = learn.train(feat, targ, steps=300, batch=4096, lr=3e-3, seed=3)
+    assert losses[-20:].mean() < losses[:5].mean()
+    held = [synth.make_system(n, 30000 + n) for n in (400, 700, 1000)]
+    plain, t_plain, _ = learn.minimize_with(held, w16, use=False)
+    pre, t_pre, xp = learn.minimize_with(held, w16, use=True)
+    it_plain = np.array([r["iterations"] for r in plain])
+    it_pre = np.array([r["iterations"] for r in pre])
+    print("plain iterations", it_plain, "preconditioned", it_pre, "time", t_plain, t_pre)
+    xs = split(xp.cpu().numpy(), held)
+    for b, s in enumerate(held):
+        assert pre[b]["status_name"] == "ok"
+        e, g = oracle_mod.energy_grad(s, xs[b])
+        assert np.abs(g).max() < 0.1 * (1 + 1e-6)
