@@ -100,6 +100,25 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def shard(seq, rank, ws):
+    """The units (systems) of one rank: a strided share, no overlap."""
+    return list(seq)[rank::ws]
+
+
+def reduce_time_units(seconds, units, device=None):
+    """(max over ranks of seconds, sum over ranks of units); identity at one
+    rank.  The only collective of the benchmark, outside the timed region."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(seconds), float(units)
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -176,18 +195,11 @@ def bench_gpu(args):
     sampler = ClockSampler(local if ws > 1 else 0)
     # ---- primary: plain FP64 ----
     S64 = ffmin.System([s], ffmin.FFMIN_FP64)
+    density64 = S64.autotune(x0)
     sampler.start()
     t64, ev64, launches, r64 = run_steps(S64, args.steps, args.warmup)
     clocks = sampler.stop()
-    step_s = max(t64) if False else sum(t64) / len(t64)
-    if ws > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([sum(t64)], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_t = float(tt.item())
-    else:
-        total_t = sum(t64)
-    total_pairs = sum(ev64) * pairs_per_eval * ws
+    total_t, total_pairs = reduce_time_units(sum(t64), sum(ev64) * pairs_per_eval, dev)
     value = total_pairs / total_t
     # e2e through the host entry point (H2D of x and D2H of the result inside)
     te2e, ev_e2e, _, _ = run_steps(S64, max(1, min(args.steps, 3)), 1, e2e=True)
@@ -198,12 +210,14 @@ def bench_gpu(args):
     S64.close()
     # ---- mixed precision, same step ----
     S32 = ffmin.System([s], ffmin.FFMIN_MIXED)
+    density32 = S32.autotune(x0)
     t32, ev32, launches32, r32 = run_steps(S32, args.steps, args.warmup)
     ms_pair32 = S32.time_pair_kernel(x0, with_grad=True, reps=20)
     S32.close()
-    value32 = sum(ev32) * pairs_per_eval * ws / sum(t32)
+    t32_tot, pairs32 = reduce_time_units(sum(t32), sum(ev32) * pairs_per_eval, dev)
+    value32 = pairs32 / t32_tot
 
-    minim = {} if args.no_minimize else minimizations(args, ffmin, synth, torch, dev)
+    minim = {} if args.no_minimize else minimizations(args, ffmin, synth, torch, dev, rank, ws)
 
     peaks = load_peaks()
     achieved_fp64 = FLOPS_PER_PAIR_EG * pairs_per_eval / (ms_pair / 1e3) / 1e12
@@ -227,6 +241,7 @@ def bench_gpu(args):
         "config": {"workload": f"{N_ATOMS}-atom chain globule (seed {SEED}), plain FP64 path, "
                                f"L-BFGS m=10 capped at {CAP_ITERS} steps per step",
                    "n_atoms": N_ATOMS, "evals_per_step": ev64[0], "l2": "flushed (256 MB write) between steps",
+                   "autotuned_items_per_block": density64,
                    "parallelism": f"replicas x{ws}"},
         "e2e": {"value": e2e_value, "unit": "pair interactions/s",
                 "h2d_bytes_per_step": 8 * 3 * N_ATOMS, "d2h_bytes_per_step": 8 * 3 * N_ATOMS},
@@ -238,6 +253,7 @@ def bench_gpu(args):
                      "flops_per_pair": FLOPS_PER_PAIR_EG, "pairs_per_launch": pairs_per_eval,
                      "peak_source": "nominal FP64 rate (see DESIGN.md)"},
         "mixed": {"value": value32, "unit": "pair interactions/s", "ms_per_step": 1e3 * sum(t32) / len(t32),
+                  "autotuned_items_per_block": density32,
                   "vs_plain_gpu": value32 / value, "pair_kernel_ms": ms_pair32,
                   "achieved_tflops": achieved_fp32, "fp32_peak_tflops_at_max_clock": fp32_peak,
                   "frac_of_fp32_peak": achieved_fp32 / fp32_peak,
@@ -254,7 +270,7 @@ def bench_gpu(args):
         dist.destroy_process_group()
 
 
-def minimizations(args, ffmin, synth, torch, dev):
+def minimizations(args, ffmin, synth, torch, dev, rank=0, ws=1):
     """Minimizations per second to |grad E|_inf < 0.1 (L-BFGS m = 10): the
     256-system batch (atom counts log-uniform in [200, 5000], seeds 1000 + b)
     in MIXED precision with and without the learned preconditioner (trained
@@ -266,11 +282,13 @@ def minimizations(args, ffmin, synth, torch, dev):
     from paper_1810_03358_gb300 import learn
     w16 = learn.load_weights()
 
-    def run(systems, prec, learned=False):
+    def run(systems, prec, learned=False, tune=True):
         S = ffmin.System(systems, prec)
         if learned:
             ffmin.ffmin_set_precond(S.handle, w16)
         x = torch.tensor(np.concatenate([q.x.reshape(-1) for q in systems]), dtype=torch.float64, device=dev)
+        if tune:
+            S.autotune(x)
         S.minimize(x.clone(), method="LBFGS", max_iter=2, use_learned_precond=int(learned))  # warm-up
         torch.cuda.synchronize()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -283,6 +301,8 @@ def minimizations(args, ffmin, synth, torch, dev):
         S.close()
         t = ev0.elapsed_time(ev1) / 1e3
         ok = sum(1 for q in r if q["status_name"] == "ok")
+        if shard_all:  # every rank ran its share: max time, summed units
+            t, ok = reduce_time_units(t, ok, dev)
         return {"n_sys": len(systems), "converged": ok, "seconds": t, "minimizations_per_s": ok / t,
                 "max_final_grad_inf": max(q["grad_inf"] for q in r),
                 "iterations_max": max(q["iterations"] for q in r),
@@ -294,10 +314,13 @@ def minimizations(args, ffmin, synth, torch, dev):
 
     out = {"learned_weights": "paper_1810_03358_gb300/precond_w16.npy" if w16 is not None else None}
     batch = synth.make_batch(256)
-    out["batch256_mixed"] = run(batch, ffmin.FFMIN_MIXED)
+    shard_all = ws > 1
+    mine = shard(batch, rank, ws)  # systems are independent: each rank minimizes its share
+    out["batch256_mixed"] = run(mine, ffmin.FFMIN_MIXED)
     if w16 is not None:
-        out["batch256_mixed_learned"] = run(batch, ffmin.FFMIN_MIXED, learned=True)
+        out["batch256_mixed_learned"] = run(mine, ffmin.FFMIN_MIXED, learned=True)
         out["batch256_learned_vs_mixed"] = ratio("batch256_mixed_learned", "batch256_mixed")
+    shard_all = False  # the comparisons below run on every rank's GPU alike
     sample = batch[:4]
     out["sample4_fp64"] = run(sample, ffmin.FFMIN_FP64)
     out["sample4_mixed"] = run(sample, ffmin.FFMIN_MIXED)
@@ -337,8 +360,9 @@ def bench_reference(args):
     from paper_1810_03358_gb300 import synth
     s = synth.make_system(N_ATOMS, SEED)
     pairs = N_ATOMS * (N_ATOMS - 1) // 2
-    for _ in range(args.warmup):
-        oracle.energy(s, s.x[:2000])  # cheap warm-up of the oracle library
+    warm = synth.make_system(2000, SEED)
+    for _ in range(args.warmup):  # untimed warm-up on a small system of the same generator
+        oracle.energy_grad(warm, warm.x)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()

@@ -193,6 +193,13 @@ ffmin_status ffmin_mlp_train(const float *feat_dev, const float *target_dev, int
                              void *cuda_stream);
 int64_t ffmin_mlp_work_floats(void);
 
+/* Autotuner: time the pair kernel (energy + gradient at x_dev) for each
+ * candidate work-item layout (3, 6, 10 or 20 (i-tile, j-chunk) items per
+ * resident block, which sets the j-chunk length of every system) and keep
+ * the fastest; *density_out = the chosen items per block.  The default
+ * before any call is 10.  Not in the paper. */
+ffmin_status ffmin_autotune(ffmin_system *sys, const double *x_dev, int32_t *density_out);
+
 /* Time the dominant pair kernel alone: reps launches at x_dev with (1) or
  * without (0) forces, CUDA events on the system's stream; *ms = mean
  * duration of one launch.  Diagnostic for roofline reporting. */

@@ -16,6 +16,10 @@
 
 using namespace ffm;
 
+// work-item densities (items per resident pair-kernel block) the autotuner tries
+static const int AUTOTUNE_DENSITIES[] = {3, 6, 10, 20};
+static const int AUTOTUNE_N = 4;
+
 namespace ffm {
 struct ParabState;
 cudaError_t launch_parab_move(const Ctx &c, ParabState *ps, int grid, cudaStream_t s);
@@ -55,7 +59,72 @@ struct ffmin_system {
     int64_t last_ticks = 0, last_launches = 0, last_pairs = 0;
     // host copies of the topology needed by the gradient-free path
     std::vector<int32_t> inc_off_h;
+    // work-item layout (rebuilt by the autotuner)
+    std::vector<Tile> tiles_h;
+    int n_bitems = 0, n_terms = 0, density = 10, grid32_max = 0, grid64_max = 0;
+    int64_t items_cap = 0;
+    Tile *d_tiles = nullptr;
+    Item *d_items = nullptr;
 };
+
+// j-chunk length of a system: a multiple of TJ, chosen so that the whole
+// batch exposes `density` work items per resident pair-kernel block (the
+// queue's tail then costs about 1/density of a block's share, against more
+// partial rows to write and sum); ffmin_autotune picks the density
+static int chunk_len(int32_t n, int64_t total_tiles, int grid, int density) {
+    int64_t want_items = (int64_t)density * grid;
+    int64_t chunks = std::max<int64_t>(1, (want_items + total_tiles - 1) / std::max<int64_t>(total_tiles, 1));
+    int64_t len = (n + chunks - 1) / chunks;
+    len = ((len + TJ - 1) / TJ) * TJ;
+    len = std::max<int64_t>(len, TJ);
+    return (int)len;
+}
+
+// Work items for a given density: bonded items first (latency-bound FP64
+// work overlapping the FP32 pair items), then (tile, j-chunk) pair items;
+// tiles' item ranges are rewritten.
+static void build_items(ffmin_system *sys, int density, std::vector<Item> &items, std::vector<Tile> &tiles) {
+    items.clear();
+    tiles = sys->tiles_h;
+    const int chunk_grid = sys->prec == FFMIN_MIXED ? sys->grid32_max : sys->grid64_max;
+    const int64_t total_tiles = (int64_t)tiles.size();
+    for (int k = 0; k < sys->n_bitems; k++) {
+        Item it{};
+        it.tile = -1;
+        it.j0 = k * BONDED_ITEM_TERMS;
+        it.nj = std::min(BONDED_ITEM_TERMS, sys->n_terms - it.j0);
+        items.push_back(it);
+    }
+    for (size_t t = 0; t < tiles.size(); t++) {
+        Tile &tl = tiles[t];
+        const int b = tl.sys;
+        const int64_t A = sys->atom_off[b];
+        const int n = sys->sys_natoms[b];
+        const int L = chunk_len(n, total_tiles, chunk_grid, density);
+        const int a0 = (int)(tl.a0 - A);
+        tl.item0 = (int)items.size();
+        int cnt = 0;
+        for (int j0 = 0; j0 < n; j0 += L) {
+            Item it{};
+            it.tile = (int)t;
+            it.j0 = (int)(A + j0);
+            it.nj = std::min(L, n - j0);
+            it.diag = (a0 >= j0 && a0 < j0 + it.nj) ? 1 : 0;
+            items.push_back(it);
+            cnt++;
+        }
+        tl.nitem = cnt;
+    }
+}
+
+static void set_item_counts(ffmin_system *sys, int n_items) {
+    sys->c.n_items = n_items;
+    sys->c.n_pair_items = n_items - sys->n_bitems;
+    // no more resident blocks than work items: idle blocks would only pay
+    // for queue atomics
+    sys->grid32 = std::max(1, std::min(sys->grid32_max, n_items));
+    sys->grid64 = std::max(1, std::min(sys->grid64_max, n_items));
+}
 
 static thread_local std::string g_create_err;
 
@@ -170,18 +239,6 @@ static bool idx_ok(const int32_t *idx, int64_t count, int32_t n) {
     return true;
 }
 
-// j-chunk length of a system: a multiple of TJ, chosen so that the whole
-// batch exposes ~10 work items per resident pair-kernel block (the queue's
-// tail then costs at most a tenth of a block's share)
-static int chunk_len(int32_t n, int64_t total_tiles, int grid) {
-    int64_t want_items = 10LL * grid;
-    int64_t chunks = std::max<int64_t>(1, (want_items + total_tiles - 1) / std::max<int64_t>(total_tiles, 1));
-    int64_t len = (n + chunks - 1) / chunks;
-    len = ((len + TJ - 1) / TJ) * TJ;
-    len = std::max<int64_t>(len, TJ);
-    return (int)len;
-}
-
 ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t precision,
                           void *cuda_stream, ffmin_system **out) {
     if (!out) return fail(nullptr, FFMIN_ERR_INVALID_ARG, "out is NULL");
@@ -225,7 +282,6 @@ ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t pre
     }
     sys->grid32 = pair_grid_size(0);
     sys->grid64 = pair_grid_size(1);
-    const int chunk_grid = precision == FFMIN_MIXED ? sys->grid32 : sys->grid64;
 
     // ---- tiles, items, per-atom data, bonded terms ----
     std::vector<Tile> tiles;
@@ -284,26 +340,13 @@ ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t pre
             dpar.push_back(make_double4_32a(v[0], v[1], v[2], v[3]));
             for (int p = 0; p < 4; p++) inc_lists[A + q[p]].push_back(make_int2((2 << 2) | p, term));
         }
-        // tiles and (tile, j-chunk) items
+        // tiles of 128 atoms (never straddling systems)
         tile0[b] = (int)tiles.size();
-        const int L = chunk_len(t.n_atoms, total_tiles, chunk_grid);
         for (int a0 = 0; a0 < t.n_atoms; a0 += TI) {
             Tile tl{};
             tl.sys = b;
             tl.a0 = (int)(A + a0);
             tl.na = std::min(TI, t.n_atoms - a0);
-            tl.item0 = (int)items.size();
-            int cnt = 0;
-            for (int j0 = 0; j0 < t.n_atoms; j0 += L) {
-                Item it{};
-                it.tile = (int)tiles.size();
-                it.j0 = (int)(A + j0);
-                it.nj = std::min(L, t.n_atoms - j0);
-                it.diag = (a0 >= j0 && a0 < j0 + it.nj) ? 1 : 0;
-                items.push_back(it);
-                cnt++;
-            }
-            tl.nitem = cnt;
             tiles.push_back(tl);
         }
         ntile[b] = (int)tiles.size() - tile0[b];
@@ -318,21 +361,17 @@ ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t pre
         for (int b = 0; b < n_sys; b++) for (int k = 0; k < tops[b].n_angles; k++) (void)k, term_sys[t++] = b;
         for (int b = 0; b < n_sys; b++) for (int k = 0; k < tops[b].n_dihedrals; k++) (void)k, term_sys[t++] = b;
     }
-    const int n_bitems = (n_terms + BONDED_ITEM_TERMS - 1) / BONDED_ITEM_TERMS;
-    {
-        std::vector<Item> all;
-        all.reserve(items.size() + n_bitems);
-        for (int k = 0; k < n_bitems; k++) {
-            Item it{};
-            it.tile = -1;
-            it.j0 = k * BONDED_ITEM_TERMS;
-            it.nj = std::min(BONDED_ITEM_TERMS, n_terms - it.j0);
-            all.push_back(it);
-        }
-        for (const Item &it : items) all.push_back(it);
-        for (Tile &tl : tiles) tl.item0 += n_bitems;
-        items.swap(all);
-    }
+    sys->n_terms = n_terms;
+    sys->n_bitems = (n_terms + BONDED_ITEM_TERMS - 1) / BONDED_ITEM_TERMS;
+    sys->tiles_h = tiles;
+    sys->sys_natoms.resize(n_sys);
+    for (int b = 0; b < n_sys; b++) sys->sys_natoms[b] = tops[b].n_atoms;
+    sys->grid32_max = sys->grid32;
+    sys->grid64_max = sys->grid64;
+    // capacity: the densest layout the autotuner may choose
+    build_items(sys, AUTOTUNE_DENSITIES[AUTOTUNE_N - 1], items, tiles);
+    sys->items_cap = (int64_t)items.size();
+    build_items(sys, sys->density, items, tiles);
     std::vector<int32_t> inc_off(total + 1, 0);
     std::vector<int2> inc;
     for (int64_t a = 0; a < total; a++) {
@@ -345,12 +384,7 @@ ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t pre
     Ctx &c = sys->c;
     c.n_sys = n_sys;
     c.n_tiles = (int)tiles.size();
-    c.n_items = (int)items.size();
-    c.n_pair_items = (int)items.size() - n_bitems;
-    // no more resident blocks than work items: idle blocks would only pay
-    // for queue atomics
-    sys->grid32 = std::max(1, std::min(sys->grid32, c.n_items));
-    sys->grid64 = std::max(1, std::min(sys->grid64, c.n_items));
+    set_item_counts(sys, (int)items.size());
     c.n_bonds = (int)bidx.size();
     c.n_angles = (int)aidx.size();
     c.n_terms = n_terms;
@@ -371,9 +405,12 @@ ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t pre
 
     Tile *d_tiles; Item *d_items;
     CKC(upload(sys, &d_tiles, tiles));
-    CKC(upload(sys, &d_items, items));
+    CKC(dalloc(sys, &d_items, (size_t)sys->items_cap));
+    CKC(cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(Item), cudaMemcpyHostToDevice, sys->stream));
     c.tiles = d_tiles;
     c.items = d_items;
+    sys->d_tiles = d_tiles;
+    sys->d_items = d_items;
     SysState *d_st;
     CKC(dalloc(sys, &d_st, n_sys));
     c.st = d_st;
@@ -388,14 +425,14 @@ ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t pre
         CKC(dalloc(sys, &c.posd, total));
         CKC(upload(sys, &d_pard, pard));
         c.pard = d_pard;
-        CKC(dalloc(sys, &c.gpd, (size_t)c.n_items * TI));
+        CKC(dalloc(sys, &c.gpd, (size_t)sys->items_cap * TI));
         if (precision == FFMIN_MIXED) {
             float2 *d_parf;
             CKC(dalloc(sys, &c.posf, total));
             CKC(dalloc(sys, &c.dispf, total));
             CKC(upload(sys, &d_parf, parf));
             c.parf = d_parf;
-            CKC(dalloc(sys, &c.gpf, (size_t)c.n_items * TI));
+            CKC(dalloc(sys, &c.gpf, (size_t)sys->items_cap * TI));
         }
     }
     int32_t *d_inc_off; int2 *d_inc, *d_bidx; double2 *d_bpar, *d_apar; int4 *d_aidx, *d_didx; double4_32a *d_dpar;
@@ -428,7 +465,6 @@ ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t pre
 
     // host mirror of the per-system state (geometry part)
     sys->hst.assign(n_sys, SysState{});
-    sys->sys_natoms.resize(n_sys);
     for (int b = 0; b < n_sys; b++) {
         SysState &S = sys->hst[b];
         std::memset(&S, 0, sizeof(S));
@@ -438,7 +474,6 @@ ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t pre
         S.ntile = ntile[b];
         S.mixed = precision == FFMIN_MIXED ? 1 : 0;
         S.mode = precision == FFMIN_MIXED ? 0 : 1;
-        sys->sys_natoms[b] = tops[b].n_atoms;
     }
     CKC(cudaMemcpyAsync(d_st, sys->hst.data(), sizeof(SysState) * n_sys, cudaMemcpyHostToDevice, sys->stream));
     CKC(cudaStreamSynchronize(sys->stream));
@@ -789,6 +824,52 @@ ffmin_status ffmin_neighbour_counts(ffmin_system *sys, const double *x_dev, int3
     // the kernel reads each system's atom range from the device state
     if ((st = upload_states(sys)) != FFMIN_OK) return st;
     CK(launch_ncount(sys->c, x_dev, counts_dev, sys->stream));
+    return leave(sys);
+}
+
+ffmin_status ffmin_autotune(ffmin_system *sys, const double *x_dev, int32_t *density_out) {
+    ffmin_status st = enter(sys);
+    if (st != FFMIN_OK) return st;
+    if (!x_dev) return fail(sys, FFMIN_ERR_INVALID_ARG, "NULL argument");
+    std::vector<Item> items;
+    std::vector<Tile> tiles;
+    float best_ms = 0.f;
+    int best = sys->density;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    for (int k = 0; k <= AUTOTUNE_N; k++) {
+        const int dens = k < AUTOTUNE_N ? AUTOTUNE_DENSITIES[k] : best;
+        build_items(sys, dens, items, tiles);
+        CK(cudaMemcpyAsync(sys->d_items, items.data(), items.size() * sizeof(Item), cudaMemcpyHostToDevice,
+                           sys->stream));
+        CK(cudaMemcpyAsync(sys->d_tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice,
+                           sys->stream));
+        set_item_counts(sys, (int)items.size());
+        if (sys->graph) {  // kernel parameters (item count, grid) changed
+            cudaGraphExecDestroy(sys->graph);
+            sys->graph = nullptr;
+        }
+        if (k == AUTOTUNE_N) break;  // the best layout is installed
+        if ((st = eval_all(sys, x_dev, EV_EG)) != FFMIN_OK) return st;
+        for (int b = 0; b < sys->n_sys; b++) sys->hst[b].ev_kind = EV_EG;
+        if ((st = upload_states(sys)) != FFMIN_OK) return st;
+        if ((st = set_counts(sys)) != FFMIN_OK) return st;
+        CK(launch_pair(sys->c, sys->grid32, sys->grid64, sys->stream));
+        CK(cudaEventRecord(e0, sys->stream));
+        for (int r = 0; r < 3; r++) CK(launch_pair(sys->c, sys->grid32, sys->grid64, sys->stream));
+        CK(cudaEventRecord(e1, sys->stream));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (k == 0 || ms < best_ms) { best_ms = ms; best = dens; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    sys->density = best;
+    for (int b = 0; b < sys->n_sys; b++) sys->hst[b].ev_kind = EV_NONE;
+    if ((st = upload_states(sys)) != FFMIN_OK) return st;
+    if (density_out) *density_out = best;
     return leave(sys);
 }
 

@@ -61,7 +61,7 @@ EXPORTS = ["ffmin_options_default", "ffmin_status_string", "ffmin_create", "ffmi
            "ffmin_energy_grad_host", "ffmin_minimize", "ffmin_minimize_host",
            "ffmin_set_precond", "ffmin_time_pair_kernel", "ffmin_last_stats",
            "ffmin_last_error", "ffmin_pair_energy_grad_noalloc", "ffmin_neighbour_counts",
-           "ffmin_mlp_train", "ffmin_mlp_work_floats"]
+           "ffmin_mlp_train", "ffmin_mlp_work_floats", "ffmin_autotune"]
 
 _lib = None
 
@@ -96,6 +96,7 @@ def lib():
     L.ffmin_last_stats.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
     L.ffmin_pair_energy_grad_noalloc.argtypes = [vp, vp, vp, vp, C.c_int32, C.c_double, vp, vp, vp]
     L.ffmin_neighbour_counts.argtypes = [vp, vp, vp]
+    L.ffmin_autotune.argtypes = [vp, vp, C.POINTER(C.c_int32)]
     L.ffmin_mlp_train.argtypes = [vp, vp, C.c_int64, C.c_int32, C.c_int32, C.c_float, C.c_uint64, vp, vp,
                                   vp, C.POINTER(C.c_float), vp, vp]
     L.ffmin_mlp_work_floats.argtypes = []
@@ -322,6 +323,9 @@ class System:
     def last_stats(self):
         return ffmin_last_stats(self.handle)
 
+    def autotune(self, x):
+        return ffmin_autotune(self.handle, x)
+
 
 def ffmin_status_string(status):
     return lib().ffmin_status_string(int(status)).decode()
@@ -374,3 +378,10 @@ def ffmin_mlp_train(feat, target, steps, batch, lr, seed, w32, adam, work, w16=N
     if st != FFMIN_OK:
         raise FfminError(st, "ffmin_mlp_train failed")
     return losses
+
+
+def ffmin_autotune(handle, x):
+    """Pick the fastest work-item layout for coordinates x; returns it."""
+    d = C.c_int32()
+    _check(lib().ffmin_autotune(C.c_void_p(handle), _dev_ptr(x, ffmin_n_atoms(handle)), C.byref(d)), handle)
+    return d.value
