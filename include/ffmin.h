@@ -200,9 +200,10 @@ int64_t ffmin_mlp_work_floats(void);
  * before any call is 10.  Not in the paper. */
 ffmin_status ffmin_autotune(ffmin_system *sys, const double *x_dev, int32_t *density_out);
 
-/* Time the dominant pair kernel alone: reps launches at x_dev with (1) or
- * without (0) forces, CUDA events on the system's stream; *ms = mean
- * duration of one launch.  Diagnostic for roofline reporting. */
+/* Time the dominant pair kernel alone: reps launches at x_dev with forces
+ * (with_grad = 1), energy only (0), or as a MIXED line-search difference
+ * trial (2), CUDA events on the system's stream; *ms = mean duration of one
+ * launch.  Diagnostic for roofline reporting. */
 ffmin_status ffmin_time_pair_kernel(ffmin_system *sys, const double *x_dev, int32_t with_grad,
                                     int32_t reps, float *ms);
 

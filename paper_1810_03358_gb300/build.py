@@ -54,7 +54,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
     os.makedirs(BUILD, exist_ok=True)
     nv = nvcc()
     common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
-              "-I", CSRC] + ARCH
+              "-I", CSRC] + ARCH + os.environ.get("FFMIN_NVCC_FLAGS", "").split()
     if ptxas_v:
         common += ["-Xptxas", "-v"]
 

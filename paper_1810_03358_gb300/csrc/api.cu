@@ -65,6 +65,9 @@ struct ffmin_system {
     int64_t items_cap = 0;
     Tile *d_tiles = nullptr;
     Item *d_items = nullptr;
+    int2 *d_sys_items = nullptr;
+    std::vector<int32_t> term_off[3];  // per-system offsets of bonds, angles, dihedrals
+    int nb_total = 0, na_total = 0;
 };
 
 // j-chunk length of a system: a multiple of TJ, chosen so that the whole
@@ -80,46 +83,62 @@ static int chunk_len(int32_t n, int64_t total_tiles, int grid, int density) {
     return (int)len;
 }
 
-// Work items for a given density: bonded items first (latency-bound FP64
-// work overlapping the FP32 pair items), then (tile, j-chunk) pair items;
-// tiles' item ranges are rewritten.
-static void build_items(ffmin_system *sys, int density, std::vector<Item> &items, std::vector<Tile> &tiles) {
+// Work items for a given density, system by system: the system's bonded
+// items (latency-bound FP64 work that overlaps the FP32 pair items), then its
+// (tile, j-chunk) pair items; every system's items are contiguous so that
+// the pair kernels can run over the active systems only.
+static void build_items(ffmin_system *sys, int density, std::vector<Item> &items, std::vector<Tile> &tiles,
+                        std::vector<int2> &sys_items) {
     items.clear();
     tiles = sys->tiles_h;
+    sys_items.assign(sys->n_sys, make_int2(0, 0));
     const int chunk_grid = sys->prec == FFMIN_MIXED ? sys->grid32_max : sys->grid64_max;
     const int64_t total_tiles = (int64_t)tiles.size();
-    for (int k = 0; k < sys->n_bitems; k++) {
-        Item it{};
-        it.tile = -1;
-        it.j0 = k * BONDED_ITEM_TERMS;
-        it.nj = std::min(BONDED_ITEM_TERMS, sys->n_terms - it.j0);
-        items.push_back(it);
-    }
-    for (size_t t = 0; t < tiles.size(); t++) {
-        Tile &tl = tiles[t];
-        const int b = tl.sys;
+    size_t t = 0;
+    for (int b = 0; b < sys->n_sys; b++) {
+        const int first = (int)items.size();
+        // bonded ranges of system b: bonds, angles, dihedrals (global indices)
+        const int starts[3] = {sys->term_off[0][b], sys->nb_total + sys->term_off[1][b],
+                               sys->nb_total + sys->na_total + sys->term_off[2][b]};
+        const int counts[3] = {sys->term_off[0][b + 1] - sys->term_off[0][b],
+                               sys->term_off[1][b + 1] - sys->term_off[1][b],
+                               sys->term_off[2][b + 1] - sys->term_off[2][b]};
+        for (int ty = 0; ty < 3; ty++) {
+            for (int k = 0; k < counts[ty]; k += BONDED_ITEM_TERMS) {
+                Item it{};
+                it.tile = -1;
+                it.j0 = starts[ty] + k;
+                it.nj = std::min(BONDED_ITEM_TERMS, counts[ty] - k);
+                it.diag = b;
+                items.push_back(it);
+            }
+        }
         const int64_t A = sys->atom_off[b];
         const int n = sys->sys_natoms[b];
         const int L = chunk_len(n, total_tiles, chunk_grid, density);
-        const int a0 = (int)(tl.a0 - A);
-        tl.item0 = (int)items.size();
-        int cnt = 0;
-        for (int j0 = 0; j0 < n; j0 += L) {
-            Item it{};
-            it.tile = (int)t;
-            it.j0 = (int)(A + j0);
-            it.nj = std::min(L, n - j0);
-            it.diag = (a0 >= j0 && a0 < j0 + it.nj) ? 1 : 0;
-            items.push_back(it);
-            cnt++;
+        for (; t < tiles.size() && tiles[t].sys == b; t++) {
+            Tile &tl = tiles[t];
+            const int a0 = (int)(tl.a0 - A);
+            tl.item0 = (int)items.size();
+            int cnt = 0;
+            for (int j0 = 0; j0 < n; j0 += L) {
+                Item it{};
+                it.tile = (int)t;
+                it.j0 = (int)(A + j0);
+                it.nj = std::min(L, n - j0);
+                it.diag = (a0 >= j0 && a0 < j0 + it.nj) ? 1 : 0;
+                items.push_back(it);
+                cnt++;
+            }
+            tl.nitem = cnt;
         }
-        tl.nitem = cnt;
+        sys_items[b] = make_int2(first, (int)items.size() - first);
     }
 }
 
 static void set_item_counts(ffmin_system *sys, int n_items) {
     sys->c.n_items = n_items;
-    sys->c.n_pair_items = n_items - sys->n_bitems;
+    sys->c.n_pair_items = n_items;
     // no more resident blocks than work items: idle blocks would only pay
     // for queue atomics
     sys->grid32 = std::max(1, std::min(sys->grid32_max, n_items));
@@ -364,14 +383,23 @@ ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t pre
     sys->n_terms = n_terms;
     sys->n_bitems = (n_terms + BONDED_ITEM_TERMS - 1) / BONDED_ITEM_TERMS;
     sys->tiles_h = tiles;
+    sys->nb_total = (int)bidx.size();
+    sys->na_total = (int)aidx.size();
+    for (int ty = 0; ty < 3; ty++) sys->term_off[ty].assign(n_sys + 1, 0);
+    for (int b = 0; b < n_sys; b++) {
+        sys->term_off[0][b + 1] = sys->term_off[0][b] + tops[b].n_bonds;
+        sys->term_off[1][b + 1] = sys->term_off[1][b] + tops[b].n_angles;
+        sys->term_off[2][b + 1] = sys->term_off[2][b] + tops[b].n_dihedrals;
+    }
+    std::vector<int2> sys_items;
     sys->sys_natoms.resize(n_sys);
     for (int b = 0; b < n_sys; b++) sys->sys_natoms[b] = tops[b].n_atoms;
     sys->grid32_max = sys->grid32;
     sys->grid64_max = sys->grid64;
     // capacity: the densest layout the autotuner may choose
-    build_items(sys, AUTOTUNE_DENSITIES[AUTOTUNE_N - 1], items, tiles);
+    build_items(sys, AUTOTUNE_DENSITIES[AUTOTUNE_N - 1], items, tiles, sys_items);
     sys->items_cap = (int64_t)items.size();
-    build_items(sys, sys->density, items, tiles);
+    build_items(sys, sys->density, items, tiles, sys_items);
     std::vector<int32_t> inc_off(total + 1, 0);
     std::vector<int2> inc;
     for (int64_t a = 0; a < total; a++) {
@@ -411,6 +439,11 @@ ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t pre
     c.items = d_items;
     sys->d_tiles = d_tiles;
     sys->d_items = d_items;
+    int2 *d_sys_items;
+    CKC(upload(sys, &d_sys_items, sys_items));
+    c.sys_items = d_sys_items;
+    sys->d_sys_items = d_sys_items;
+    CKC(dalloc(sys, &c.act, 2 * (2 * (size_t)n_sys + 2)));
     SysState *d_st;
     CKC(dalloc(sys, &d_st, n_sys));
     c.st = d_st;
@@ -792,11 +825,17 @@ ffmin_status ffmin_time_pair_kernel(ffmin_system *sys, const double *x_dev, int3
                                     float *ms) {
     ffmin_status st = enter(sys);
     if (st != FFMIN_OK) return st;
-    if (!x_dev || !ms || reps < 1) return fail(sys, FFMIN_ERR_INVALID_ARG, "bad argument");
+    if (!x_dev || !ms || reps < 1 || with_grad < 0 || with_grad > 2 ||
+        (with_grad == 2 && sys->prec != FFMIN_MIXED))
+        return fail(sys, FFMIN_ERR_INVALID_ARG, "bad argument");
     // one full evaluation leaves the positions of x in the pair-kernel inputs
-    st = eval_all(sys, x_dev, with_grad ? EV_EG : EV_E);
+    st = eval_all(sys, x_dev, with_grad == 1 ? EV_EG : EV_E);
     if (st != FFMIN_OK) return st;
-    for (int b = 0; b < sys->n_sys; b++) sys->hst[b].ev_kind = with_grad ? EV_EG : EV_E;
+    if (with_grad == 2) CK(cudaMemsetAsync(sys->c.dispf, 0, sizeof(float4) * sys->n_atoms, sys->stream));
+    for (int b = 0; b < sys->n_sys; b++) {
+        sys->hst[b].ev_kind = with_grad == 1 ? EV_EG : EV_E;
+        sys->hst[b].ev_delta = with_grad == 2 ? 1 : 0;
+    }
     if ((st = upload_states(sys)) != FFMIN_OK) return st;
     if ((st = set_counts(sys)) != FFMIN_OK) return st;
     cudaEvent_t e0, e1;
@@ -812,7 +851,10 @@ ffmin_status ffmin_time_pair_kernel(ffmin_system *sys, const double *x_dev, int3
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     *ms = t / (float)reps;
-    for (int b = 0; b < sys->n_sys; b++) sys->hst[b].ev_kind = EV_NONE;
+    for (int b = 0; b < sys->n_sys; b++) {
+        sys->hst[b].ev_kind = EV_NONE;
+        sys->hst[b].ev_delta = 0;
+    }
     if ((st = upload_states(sys)) != FFMIN_OK) return st;
     return leave(sys);
 }
@@ -833,6 +875,7 @@ ffmin_status ffmin_autotune(ffmin_system *sys, const double *x_dev, int32_t *den
     if (!x_dev) return fail(sys, FFMIN_ERR_INVALID_ARG, "NULL argument");
     std::vector<Item> items;
     std::vector<Tile> tiles;
+    std::vector<int2> sys_items;
     float best_ms = 0.f;
     int best = sys->density;
     cudaEvent_t e0, e1;
@@ -840,9 +883,11 @@ ffmin_status ffmin_autotune(ffmin_system *sys, const double *x_dev, int32_t *den
     CK(cudaEventCreate(&e1));
     for (int k = 0; k <= AUTOTUNE_N; k++) {
         const int dens = k < AUTOTUNE_N ? AUTOTUNE_DENSITIES[k] : best;
-        build_items(sys, dens, items, tiles);
+        build_items(sys, dens, items, tiles, sys_items);
         CK(cudaMemcpyAsync(sys->d_items, items.data(), items.size() * sizeof(Item), cudaMemcpyHostToDevice,
                            sys->stream));
+        CK(cudaMemcpyAsync(sys->d_sys_items, sys_items.data(), sys_items.size() * sizeof(int2),
+                           cudaMemcpyHostToDevice, sys->stream));
         CK(cudaMemcpyAsync(sys->d_tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice,
                            sys->stream));
         set_item_counts(sys, (int)items.size());

@@ -51,7 +51,7 @@ enum Phase : int {
 };
 
 // a pair item (i-tile, j-chunk); tile < 0 marks a bonded item whose j0, nj
-// is a range of bonded terms
+// is a range of bonded terms (of one type and one system, diag = system)
 struct Item { int32_t tile, j0, nj, diag; };
 constexpr int BONDED_ITEM_TERMS = 64;
 
@@ -152,6 +152,9 @@ struct Ctx {
     const double4_32a *dpar;
     int32_t n_bonds, n_angles, n_terms, n_pair_items;  // batch totals; bonded items follow pair items
     const int32_t *term_sys;  // [n_terms] system of each bonded term
+    const int2 *sys_items;  // [n_sys] (first, count) of each system's work items (contiguous)
+    int32_t *act;           // per pair-kernel mode m: [m * (2 n_sys + 2)]: active systems, their
+                            // items, item prefix [n_sys], system ids [n_sys] (rebuilt every launch)
     double *te;             // [n_terms] energy of each bonded term
     double *tg;             // [2 nb + 3 na + 4 nd][3] gradient of each term at each position
     // reductions

@@ -134,8 +134,18 @@ __device__ __forceinline__ void sweep_delta(const float4 *__restrict__ sp, const
 // NT threads per block, IPT i-atoms per thread, NT * IPT == TI (one tile).
 // the register cap (64 per thread) keeps the pair sweep at 16 (FP32) or 8
 // (FP64) resident blocks per SM; the rarely-run bonded items may spill
+// FP32 kernel shape: i-atoms per thread and resident blocks per SM (the
+// register cap follows: 65536 / (blocks * threads))
+#ifndef FFMIN_F32_IPT
+#define FFMIN_F32_IPT 2
+#endif
+#ifndef FFMIN_F32_MINBLOCKS
+#define FFMIN_F32_MINBLOCKS (1024 / TI * FFMIN_F32_IPT)
+#endif
 template <typename T, int NT, int IPT>
-__global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 16 : 8)) k_pair(Ctx c) {
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? FFMIN_F32_MINBLOCKS : 8)) k_pair(Ctx c);
+template <typename T, int NT, int IPT>
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? FFMIN_F32_MINBLOCKS : 8)) k_pair(Ctx c) {
     static_assert(NT * IPT == TI, "a block covers one i-tile");
     using V4 = typename VT<T>::V4;
     using V2 = typename VT<T>::V2;
@@ -153,14 +163,32 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 16 : 8)) k_pair(Ctx c) {
     }
     constexpr int MODE = sizeof(T) == 4 ? 0 : 1;
     constexpr int CNT = MODE == 0 ? CNT_PAIR : CNT_PAIR64;
-    if (c.nmode[MODE] == 0) return;  // no system evaluates in this precision
+    // the queue runs over the items of the systems evaluating in this
+    // precision only (active list rebuilt before every launch)
+    const int32_t *A = c.act + MODE * (2 * c.n_sys + 2);
+    const int n_act = A[0], total = A[1];
+    if (total == 0) return;
+    const int32_t *aoff = A + 2, *asys = A + 2 + c.n_sys;
     const int tid = threadIdx.x;
     for (;;) {
-        if (tid == 0) s_item = (int)atomicAdd(&c.counters[CNT], 1u);
+        if (tid == 0) {
+            const int q = (int)atomicAdd(&c.counters[CNT], 1u);
+            if (q < total) {  // last active system whose first item is <= q
+                int lo = 0, hi = n_act - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (aoff[mid] <= q) lo = mid;
+                    else hi = mid - 1;
+                }
+                s_item = c.sys_items[asys[lo]].x + (q - aoff[lo]);
+            } else {
+                s_item = -1;
+            }
+        }
         __syncthreads();
         const int it = s_item;
         __syncthreads();
-        if (it >= c.n_items) break;
+        if (it < 0) break;
         const Item I = c.items[it];
         if (I.tile < 0) {  // bonded terms (FP64), overlapping the pair items of other warps
             bonded_item(c, I.j0, I.nj, MODE);
@@ -248,9 +276,9 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 16 : 8)) k_pair(Ctx c) {
 
 // launch shapes: FP32 two i-atoms per thread (halves shared-memory loads
 // per pair), FP64 one (the FP64 pipe, not the loads, is the limit)
-#define K_F32 k_pair<float, 64, 2>
+constexpr int NT_F32 = TI / FFMIN_F32_IPT, NT_F64 = 128;
+#define K_F32 k_pair<float, NT_F32, FFMIN_F32_IPT>
 #define K_F64 k_pair<double, 128, 1>
-constexpr int NT_F32 = 64, NT_F64 = 128;
 
 int pair_grid_size(int mode) {
     int dev = 0, sms = 0, per = 0;
@@ -264,7 +292,51 @@ int pair_grid_size(int mode) {
     return sms * per;
 }
 
+// Active lists for the two pair kernels: for each precision mode, the
+// systems with an evaluation request in that mode and the prefix of their
+// item counts (one block; exclusive scan in chunks of the block size).
+__global__ void __launch_bounds__(256) k_activelist(Ctx c) {
+    __shared__ int cnt[256], sy[256];
+    __shared__ int base_items, base_sys;
+    for (int m = 0; m < 2; m++) {
+        int32_t *A = c.act + m * (2 * c.n_sys + 2);
+        if (threadIdx.x == 0) { base_items = 0; base_sys = 0; }
+        __syncthreads();
+        for (int b0 = 0; b0 < c.n_sys; b0 += 256) {
+            const int b = b0 + threadIdx.x;
+            int n = 0;
+            if (b < c.n_sys) {
+                const SysState &S = c.st[b];
+                if (S.ev_kind != EV_NONE && S.mode == m) n = c.sys_items[b].y;
+            }
+            cnt[threadIdx.x] = n;
+            sy[threadIdx.x] = n > 0 ? 1 : 0;
+            __syncthreads();
+            if (threadIdx.x == 0) {  // serial scan of this chunk (fixed order)
+                int ib = base_items, sb = base_sys;
+                for (int k = 0; k < 256 && b0 + k < c.n_sys; k++) {
+                    if (cnt[k] > 0) {
+                        A[2 + sb] = ib;
+                        A[2 + c.n_sys + sb] = b0 + k;
+                        ib += cnt[k];
+                        sb++;
+                    }
+                }
+                base_items = ib;
+                base_sys = sb;
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            A[0] = base_sys;
+            A[1] = base_items;
+        }
+        __syncthreads();
+    }
+}
+
 cudaError_t launch_pair(const Ctx &c, int grid32, int grid64, cudaStream_t s) {
+    k_activelist<<<1, 256, 0, s>>>(c);
     // fresh work queues (counters CNT_PAIR and CNT_PAIR64)
     cudaError_t e0 = cudaMemsetAsync(c.counters + CNT_PAIR, 0, sizeof(unsigned), s);
     if (e0 == cudaSuccess) e0 = cudaMemsetAsync(c.counters + CNT_PAIR64, 0, sizeof(unsigned), s);
