@@ -34,8 +34,33 @@ METRIC = "E+grad pair interactions/s and minimizations/s to ‖∇E‖∞<0.1, v
 N_ATOMS = 30000
 SEED = 3
 CAP_ITERS = 10
-FLOPS_PER_PAIR_EG = 35.0   # nominal FP32-style count, FMA = 2
-FLOPS_PER_PAIR_E = 23.0
+# flops per evaluated (ordered) pair of the row sweep, FMA = 2, rsqrt = 1:
+# d 3, r^2 5, r^-1 1, r^-2 1, e_cul 2, r^-6 2, C6/C12 2, t1 2, E acc 3,
+# t2 2, F 3, grad acc 6 (E only: the first 21).  The sweep evaluates each
+# unordered pair twice (rows i and j), N(N-1) evaluations per launch.
+FLOPS_PER_PAIR_EG = 32.0
+FLOPS_PER_PAIR_E = 21.0
+# ALU peaks derived from unit counts at the maximum SM clock: FP32 152 SMs x
+# 128 lanes x 2 flops; FP64 152 SMs x 2 FMA per clock x 2 flops (the GB300
+# nominal 1.25 TFLOP/s at 2,070 MHz)
+FP32_LANES_X2 = 152 * 128 * 2
+FP64_LANES_X2 = 152 * 2 * 2
+PROFILE_SUMMARY = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles",
+                               "pair_kernels_30k.md")
+
+
+def profiled_traffic(kernel):
+    """DRAM bytes (read + write) of one launch of `kernel` from the committed
+    ncu summary (a line 'traffic_bytes <kernel>: <bytes>'), else None."""
+    try:
+        with open(PROFILE_SUMMARY) as f:
+            for ln in f:
+                ln = ln.strip().strip("`")
+                if ln.startswith(f"traffic_bytes {kernel}:"):
+                    return int(ln.split(":")[1])
+    except OSError:
+        pass
+    return None
 
 
 def dist_env():
@@ -219,12 +244,16 @@ def bench_gpu(args):
 
     minim = {} if args.no_minimize else minimizations(args, ffmin, synth, torch, dev, rank, ws)
 
-    peaks = load_peaks()
-    achieved_fp64 = FLOPS_PER_PAIR_EG * pairs_per_eval / (ms_pair / 1e3) / 1e12
-    achieved_fp32 = FLOPS_PER_PAIR_EG * pairs_per_eval / (ms_pair32 / 1e3) / 1e12
-    sm_clock = clocks.get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median") or 2070.0
-    fp32_peak = 152 * 128 * 2 * 2070e6 / 1e12
-    fp64_peak = float(os.environ.get("FFMIN_FP64_PEAK_TFLOPS", "1.25"))
+    sm_max_mhz = float(load_peaks().get("sm_max_mhz", 2070.0))
+    fp32_derived = FP32_LANES_X2 * sm_max_mhz * 1e6 / 1e12
+    fp64_derived = FP64_LANES_X2 * sm_max_mhz * 1e6 / 1e12
+    # measured FMA peaks of this GPU (independent FMA chains on every SM)
+    fp32_peak = ffmin.ffmin_alu_peak(ffmin.FFMIN_MIXED, reps=20)
+    fp64_peak = ffmin.ffmin_alu_peak(ffmin.FFMIN_FP64, reps=20)
+    evaluated = N_ATOMS * (N_ATOMS - 1)  # ordered pairs evaluated per launch (row sweep)
+    achieved_fp64 = FLOPS_PER_PAIR_EG * evaluated / (ms_pair / 1e3) / 1e12
+    achieved_fp64_e = FLOPS_PER_PAIR_E * evaluated / (ms_pair_e / 1e3) / 1e12
+    achieved_fp32 = FLOPS_PER_PAIR_EG * evaluated / (ms_pair32 / 1e3) / 1e12
     line = {
         "metric": METRIC,
         "value": value,
@@ -248,16 +277,25 @@ def bench_gpu(args):
         "gpu_launches": int(launches),
         "clocks": clocks,
         "roofline": {"bound": "alu", "achieved": achieved_fp64, "peak": fp64_peak, "unit": "TFLOP/s",
-                     "frac": achieved_fp64 / fp64_peak, "traffic": None,
-                     "kernel": "k_pair<double> (E+grad)", "ms_per_launch": ms_pair,
-                     "flops_per_pair": FLOPS_PER_PAIR_EG, "pairs_per_launch": pairs_per_eval,
-                     "peak_source": "nominal FP64 rate (see DESIGN.md)"},
+                     "frac": achieved_fp64 / fp64_peak,
+                     "traffic": profiled_traffic("k_pair<double,128,1> E+grad"),
+                     "kernel": "k_pair<double,128,1> E+grad",
+                     "ms_per_launch": ms_pair, "flops_per_evaluated_pair": FLOPS_PER_PAIR_EG,
+                     "evaluated_pairs_per_launch": evaluated,
+                     "peak_source": "measured FP64 FMA-chain probe (ffmin_alu_peak)",
+                     "peak_derived": fp64_derived,
+                     "e_only": {"ms_per_launch": ms_pair_e, "achieved": achieved_fp64_e,
+                                "frac": achieved_fp64_e / fp64_peak}},
         "mixed": {"value": value32, "unit": "pair interactions/s", "ms_per_step": 1e3 * sum(t32) / len(t32),
                   "autotuned_items_per_block": density32,
-                  "vs_plain_gpu": value32 / value, "pair_kernel_ms": ms_pair32,
-                  "achieved_tflops": achieved_fp32, "fp32_peak_tflops_at_max_clock": fp32_peak,
-                  "frac_of_fp32_peak": achieved_fp32 / fp32_peak,
-                  "final_energy": r32["energy"], "final_energy_fp64": r64["energy"]},
+                  "vs_plain_gpu": value32 / value,
+                  "final_energy": r32["energy"], "final_energy_fp64": r64["energy"],
+                  "roofline": {"bound": "alu", "kernel": "k_pair<float,64,2> E+grad",
+                               "achieved": achieved_fp32, "peak": fp32_peak, "unit": "TFLOP/s",
+                               "frac": achieved_fp32 / fp32_peak, "ms_per_launch": ms_pair32,
+                               "traffic": profiled_traffic("k_pair<float,64,2> E+grad"),
+                               "peak_source": "measured FP32 FMA-chain probe (ffmin_alu_peak)",
+                               "peak_derived": fp32_derived}},
         "pair_kernel_e_only_ms": ms_pair_e,
         "minimize": minim,
     }
@@ -387,7 +425,10 @@ def profile_run(args):
     """Small fixed workloads for ncu captures.  Default: one E + grad E of
     the 30,000-atom globule with the MIXED pair kernel, then one with FP64.
     --profile-minimize K: a K-step MIXED L-BFGS run of the 3,334-atom globule
-    (every kernel of the minimizer pipeline)."""
+    (every kernel of the minimizer pipeline).  --profile-batch K: K steps of
+    the 256-system batch.  --profile-vectors K: K FP64 L-BFGS steps of 1,024
+    systems of 500 atoms (the update and direction kernels at full history)."""
+    import numpy as np
     import torch
     from paper_1810_03358_gb300 import build as gbuild
     gbuild.build()
@@ -405,6 +446,29 @@ def profile_run(args):
         torch.cuda.synchronize()
         st = S.last_stats()
         print("profile-batch", st, "ms", ev0.elapsed_time(ev1), "ms/tick", ev0.elapsed_time(ev1) / st["ticks"])
+        S.close()
+        return
+    if args.profile_vectors:
+        # 1,024 systems of 500 atoms (512,000 atoms, vectors of 12.3 MB; 64
+        # chains, each under 16 coordinate jitters): FP64
+        # L-BFGS m = 10 for profile_vectors iterations; all systems take the
+        # same number of line-search trials, so after 10 iterations every
+        # tick's update / direction launches cover every atom with a full
+        # history (the vector-kernel workload)
+        import dataclasses
+        base = [synth.make_system(500, 50000 + b) for b in range(64)]
+        systems = []
+        for b in range(1024):  # 64 chains x 16 jitters of the reference coordinates
+            s0 = base[b % 64]
+            jr = np.random.default_rng(60000 + b)
+            systems.append(dataclasses.replace(s0, x=np.ascontiguousarray(
+                s0.x_ref + jr.normal(0.0, synth.JITTER_SIGMA, size=s0.x_ref.shape))))
+        S = ffmin.System(systems, ffmin.FFMIN_FP64)
+        x = torch.tensor(np.concatenate([s.x.reshape(-1) for s in systems]), dtype=torch.float64,
+                         device="cuda")
+        r = S.minimize(x.clone(), method="LBFGS", max_iter=args.profile_vectors)
+        torch.cuda.synchronize()
+        print("profile-vectors", S.last_stats(), sorted({q["iterations"] for q in r}))
         S.close()
         return
     if args.profile_minimize:
@@ -445,6 +509,7 @@ def main():
     ap.add_argument("--profile-atoms", type=int, default=N_ATOMS)
     ap.add_argument("--profile-minimize", type=int, default=0)
     ap.add_argument("--profile-batch", type=int, default=0)
+    ap.add_argument("--profile-vectors", type=int, default=0)
     args = ap.parse_args()
     if args.profile:
         profile_run(args)

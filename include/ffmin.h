@@ -207,6 +207,13 @@ ffmin_status ffmin_autotune(ffmin_system *sys, const double *x_dev, int32_t *den
 ffmin_status ffmin_time_pair_kernel(ffmin_system *sys, const double *x_dev, int32_t with_grad,
                                     int32_t reps, float *ms);
 
+/* Measured ALU peak of the current device in TFLOP/s (FMA = 2 flops):
+ * independent FP32 (precision = FFMIN_MIXED) or FP64 (FFMIN_FP64) FMA
+ * chains on every SM, reps timed launches on the default stream after three
+ * warm-up launches.  Allocates and frees a small output buffer.  The
+ * denominator of the pair kernels' roofline; not part of the paper. */
+ffmin_status ffmin_alu_peak(int32_t precision, int32_t reps, double *tflops);
+
 /* Work done by the last ffmin_minimize: pair kernel launches and device
  * evaluation rounds; n_kernel_launches counts every kernel launched. */
 ffmin_status ffmin_last_stats(const ffmin_system *sys, int64_t *ticks,

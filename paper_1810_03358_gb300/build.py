@@ -24,6 +24,7 @@ UNITS = {
     "parab.cu": ["-fmad=false"],
     "mlp.cu": [],
     "noalloc.cu": [],
+    "peak.cu": [],
     "api.cu": [],
 }
 

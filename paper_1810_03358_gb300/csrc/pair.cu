@@ -132,15 +132,17 @@ __device__ __forceinline__ void sweep_delta(const float4 *__restrict__ sp, const
 }
 
 // NT threads per block, IPT i-atoms per thread, NT * IPT == TI (one tile).
-// the register cap (64 per thread) keeps the pair sweep at 16 (FP32) or 8
-// (FP64) resident blocks per SM; the rarely-run bonded items may spill
-// FP32 kernel shape: i-atoms per thread and resident blocks per SM (the
-// register cap follows: 65536 / (blocks * threads))
+// Register caps: the FP32 kernel (2 i-atoms per thread) runs at 12 resident
+// 64-thread blocks per SM (80 registers; measured on GB300 faster than 16
+// blocks at 64 registers and than 4 i-atoms per thread), the FP64 kernel at
+// 8 blocks of 128 (64 registers); the rarely-run bonded items may spill.
+// FFMIN_F32_IPT / FFMIN_F32_MINBLOCKS override the FP32 shape (the register
+// cap follows: 65536 / (blocks * threads)).
 #ifndef FFMIN_F32_IPT
 #define FFMIN_F32_IPT 2
 #endif
 #ifndef FFMIN_F32_MINBLOCKS
-#define FFMIN_F32_MINBLOCKS (1024 / TI * FFMIN_F32_IPT)
+#define FFMIN_F32_MINBLOCKS (768 / TI * FFMIN_F32_IPT)
 #endif
 template <typename T, int NT, int IPT>
 __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? FFMIN_F32_MINBLOCKS : 8)) k_pair(Ctx c);
@@ -293,11 +295,17 @@ int pair_grid_size(int mode) {
 }
 
 // Active lists for the two pair kernels: for each precision mode, the
-// systems with an evaluation request in that mode and the prefix of their
-// item counts (one block; exclusive scan in chunks of the block size).
+// systems with an evaluation request in that mode and the exclusive prefix
+// of their item counts, in system order (one block; warp-shuffle scans over
+// chunks of 256 systems).  The block also resets both work-queue counters.
 __global__ void __launch_bounds__(256) k_activelist(Ctx c) {
-    __shared__ int cnt[256], sy[256];
+    __shared__ int wsum_i[8], wsum_s[8];
     __shared__ int base_items, base_sys;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        c.counters[CNT_PAIR] = 0;
+        c.counters[CNT_PAIR64] = 0;
+    }
     for (int m = 0; m < 2; m++) {
         int32_t *A = c.act + m * (2 * c.n_sys + 2);
         if (threadIdx.x == 0) { base_items = 0; base_sys = 0; }
@@ -309,22 +317,23 @@ __global__ void __launch_bounds__(256) k_activelist(Ctx c) {
                 const SysState &S = c.st[b];
                 if (S.ev_kind != EV_NONE && S.mode == m) n = c.sys_items[b].y;
             }
-            cnt[threadIdx.x] = n;
-            sy[threadIdx.x] = n > 0 ? 1 : 0;
-            __syncthreads();
-            if (threadIdx.x == 0) {  // serial scan of this chunk (fixed order)
-                int ib = base_items, sb = base_sys;
-                for (int k = 0; k < 256 && b0 + k < c.n_sys; k++) {
-                    if (cnt[k] > 0) {
-                        A[2 + sb] = ib;
-                        A[2 + c.n_sys + sb] = b0 + k;
-                        ib += cnt[k];
-                        sb++;
-                    }
-                }
-                base_items = ib;
-                base_sys = sb;
+            const int f = n > 0 ? 1 : 0;
+            int si = n, ss = f;  // inclusive scans within the warp
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int ti = __shfl_up_sync(0xffffffffu, si, o), ts = __shfl_up_sync(0xffffffffu, ss, o);
+                if (lane >= o) { si += ti; ss += ts; }
             }
+            if (lane == 31) { wsum_i[warp] = si; wsum_s[warp] = ss; }
+            __syncthreads();
+            int pi = base_items + si - n, ps = base_sys + ss - f;
+            for (int w = 0; w < warp; w++) { pi += wsum_i[w]; ps += wsum_s[w]; }
+            if (f) {
+                A[2 + ps] = pi;
+                A[2 + c.n_sys + ps] = b;
+            }
+            __syncthreads();
+            if (threadIdx.x == 255) { base_items = pi + n; base_sys = ps + f; }
             __syncthreads();
         }
         if (threadIdx.x == 0) {
@@ -336,11 +345,7 @@ __global__ void __launch_bounds__(256) k_activelist(Ctx c) {
 }
 
 cudaError_t launch_pair(const Ctx &c, int grid32, int grid64, cudaStream_t s) {
-    k_activelist<<<1, 256, 0, s>>>(c);
-    // fresh work queues (counters CNT_PAIR and CNT_PAIR64)
-    cudaError_t e0 = cudaMemsetAsync(c.counters + CNT_PAIR, 0, sizeof(unsigned), s);
-    if (e0 == cudaSuccess) e0 = cudaMemsetAsync(c.counters + CNT_PAIR64, 0, sizeof(unsigned), s);
-    if (e0 != cudaSuccess) return e0;
+    k_activelist<<<1, 256, 0, s>>>(c);  // also gives both pair kernels fresh work queues
     if (c.prec == FFMIN_MIXED) {
         K_F32<<<grid32, NT_F32, 0, s>>>(c);
         cudaError_t e = cudaGetLastError();

@@ -61,7 +61,7 @@ EXPORTS = ["ffmin_options_default", "ffmin_status_string", "ffmin_create", "ffmi
            "ffmin_energy_grad_host", "ffmin_minimize", "ffmin_minimize_host",
            "ffmin_set_precond", "ffmin_time_pair_kernel", "ffmin_last_stats",
            "ffmin_last_error", "ffmin_pair_energy_grad_noalloc", "ffmin_neighbour_counts",
-           "ffmin_mlp_train", "ffmin_mlp_work_floats", "ffmin_autotune"]
+           "ffmin_mlp_train", "ffmin_mlp_work_floats", "ffmin_autotune", "ffmin_alu_peak"]
 
 _lib = None
 
@@ -86,6 +86,7 @@ def lib():
     L.ffmin_n_atoms.restype = C.c_int64
     L.ffmin_atom_offset.argtypes = [vp, C.c_int32]
     L.ffmin_atom_offset.restype = C.c_int64
+    L.ffmin_alu_peak.argtypes = [C.c_int32, C.c_int32, _dp]
     L.ffmin_energy.argtypes = [vp, vp, _dp]
     L.ffmin_energy_grad.argtypes = [vp, vp, _dp, vp]
     L.ffmin_energy_grad_host.argtypes = [vp, _dp, _dp, _dp]
@@ -269,6 +270,13 @@ def ffmin_time_pair_kernel(handle, x, with_grad=True, reps=10):
                                       int(with_grad), int(reps), C.byref(ms))
     _check(st, handle)
     return ms.value
+
+
+def ffmin_alu_peak(precision, reps=10):
+    """Measured FP32 (precision = FFMIN_MIXED) or FP64 FMA peak, TFLOP/s."""
+    t = C.c_double()
+    _check(lib().ffmin_alu_peak(int(precision), int(reps), C.byref(t)))
+    return t.value
 
 
 def ffmin_last_stats(handle):
