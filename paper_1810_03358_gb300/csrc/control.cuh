@@ -565,7 +565,12 @@ __device__ void lbfgs_pass1(SysState &S, int use_d) {
 }
 
 // reductions of the update kernel (U_PUSH)
-enum { RU_SY = 0, RU_YY, RU_SG, RU_SJY, RU_SJG = RU_SJY + NRING, RU_N = RU_SJG + NRING };
+// <s,y>, <y,y>, <s,g+>, then (<s_j,y>, <s_j,g+>) interleaved for the nS
+// committed pairs, so a push reduces only 3 + 2 nS values
+enum { RU_SY = 0, RU_YY, RU_SG, RU_N = 3 + 2 * NRING };
+__host__ __device__ constexpr int ru_sjy(int j) { return 3 + 2 * j; }
+__host__ __device__ constexpr int ru_sjg(int j) { return 4 + 2 * j; }
+__host__ __device__ constexpr int ru_count(int nS) { return 3 + 2 * nS; }
 
 __device__ void on_update_done(const Ctx &c, SysState &S, const double *v) {
     const int op = S.upd.op;
@@ -577,7 +582,7 @@ __device__ void on_update_done(const Ctx &c, SysState &S, const double *v) {
     }
     if (op != U_PUSH) return;
     const int nS = S.upd.nS;
-    for (int k = 0; k < nS; k++) S.sg[S.upd.sS[k]] = v[RU_SJG + k];
+    for (int k = 0; k < nS; k++) S.sg[S.upd.sS[k]] = v[ru_sjg(k)];
     const double sy = v[RU_SY];
     if (sy > 0.0) {
         if (S.ring_count == S.m) {  // drop the oldest pair
@@ -587,7 +592,7 @@ __device__ void on_update_done(const Ctx &c, SysState &S, const double *v) {
         const int st = S.upd.stage;
         for (int k = 0; k < nS; k++) {
             const int a = S.upd.sS[k];
-            S.SY[a][st] = v[RU_SJY + k];
+            S.SY[a][st] = v[ru_sjy(k)];
         }
         S.rho[st] = 1.0 / sy;
         S.yy[st] = v[RU_YY];

@@ -26,6 +26,12 @@
 
 namespace ffm {
 
+// <a, b> of two 3-vectors with explicit FMA (this unit is compiled without
+// implicit contraction; the vector kernels are FP64-pipe bound)
+__device__ __forceinline__ double dot3_fma(const double *a, const double *b) {
+    return fma(a[0], b[0], fma(a[1], b[1], a[2] * b[2]));
+}
+
 // ---------------------------------------------------------------- prepare
 __global__ void __launch_bounds__(TI) k_prepare(Ctx c) {
     const Tile t = c.tiles[blockIdx.x];
@@ -105,16 +111,16 @@ __global__ void __launch_bounds__(TI) k_finalize(Ctx c) {
             gt[0] = g0; gt[1] = g1; gt[2] = g2;
             const double *G = vslot(c, V_G) + 3 * a;
             const double *R = vslot(c, V_R) + 3 * a;
-            v[RF_GG] = g0 * g0 + g1 * g1 + g2 * g2;
+            v[RF_GG] = fma(g0, g0, fma(g1, g1, g2 * g2));
             v[RF_GINF] = fmax(fabs(g0), fmax(fabs(g1), fabs(g2)));
-            v[RF_GTG] = g0 * G[0] + g1 * G[1] + g2 * G[2];
-            v[RF_GTR] = g0 * R[0] + g1 * R[1] + g2 * R[2];
+            v[RF_GTG] = fma(g0, G[0], fma(g1, G[1], g2 * G[2]));
+            v[RF_GTR] = fma(g0, R[0], fma(g1, R[1], g2 * R[2]));
             bad = bad || !isfinite(g0) || !isfinite(g1) || !isfinite(g2);
         }
         v[RF_BAD] = bad ? 1.0 : 0.0;
     }
     const unsigned maxmask = (1u << RF_GINF) | (1u << RF_BAD);
-    block_reduce_store<RF_N>(v, maxmask, &c.red[(int64_t)blockIdx.x * NRED]);
+    block_reduce_columns<RF_N>(v, RF_N, maxmask, &c.red[(int64_t)blockIdx.x * NRED]);
     if (c.sep_reduce || !last_block(&c.counters[CNT_FIN])) return;
     last_block_systems<RF_N>(
         c, RF_N, maxmask, [](const SysState &S) { return S.ev_kind != EV_NONE; },
@@ -145,8 +151,8 @@ __global__ void __launch_bounds__(TI) k_update(Ctx c) {
                 Ss[k] = s[k];
                 Ys[k] = y[k];
             }
-            v[RU_SY] = s[0] * y[0] + s[1] * y[1] + s[2] * y[2];
-            v[RU_YY] = y[0] * y[0] + y[1] * y[1] + y[2] * y[2];
+            v[RU_SY] = dot3_fma(s, y);
+            v[RU_YY] = dot3_fma(y, y);
             if (S.rec_ptr && S.rec_every > 0 && S.iter % S.rec_every == 0) {
                 const int slot = S.iter / S.rec_every - 1;
                 if (slot < S.rec_slots) {
@@ -157,19 +163,19 @@ __global__ void __launch_bounds__(TI) k_update(Ctx c) {
                     r[3] = 1.0;
                 }
             }
-            v[RU_SG] = s[0] * GT[0] + s[1] * GT[1] + s[2] * GT[2];
+            v[RU_SG] = dot3_fma(s, GT);
             const int nS = S.upd.nS;
 #pragma unroll
             for (int j = 0; j < NRING; j++) {
                 if (j < nS) {
                     const double *sj = vslot(c, V_S0 + S.upd.sS[j]) + off;
-                    v[RU_SJY + j] = sj[0] * y[0] + sj[1] * y[1] + sj[2] * y[2];
-                    v[RU_SJG + j] = sj[0] * GT[0] + sj[1] * GT[1] + sj[2] * GT[2];
+                    v[ru_sjy(j)] = dot3_fma(sj, y);
+                    v[ru_sjg(j)] = dot3_fma(sj, GT);
                 }
             }
             for (int k = 0; k < 3; k++) { X[k] = XT[k]; G[k] = GT[k]; }
         }
-        block_reduce_store_many(v, RU_N, &c.red[(int64_t)blockIdx.x * NRED]);
+        block_reduce_columns<RU_N>(v, ru_count(S.upd.nS), 0u, &c.red[(int64_t)blockIdx.x * NRED]);
     } else if (op != U_NONE && i < t.na) {
         const int64_t off = 3 * (int64_t)(t.a0 + i);
         double *X = vslot(c, V_X) + off, *G = vslot(c, V_G) + off, *W = vslot(c, V_W) + off;
@@ -210,7 +216,7 @@ __global__ void __launch_bounds__(TI) k_update(Ctx c) {
     last_block_systems<RU_N>(
         c, RU_N, 0u, [](const SysState &S) { return S.upd.op != U_NONE; },
         [&](SysState &S, const double *tot) { on_update_done(c, S, tot); },
-        [](const SysState &S) { return S.upd.op == U_PUSH ? RU_N : 0; });
+        [](const SysState &S) { return S.upd.op == U_PUSH ? ru_count(S.upd.nS) : 0; });
     __syncthreads();
     if (threadIdx.x == 0) c.counters[CNT_UPD] = 0;
 }
@@ -240,18 +246,18 @@ __global__ void __launch_bounds__(TI) k_dir(Ctx c) {
         for (int k = 0; k < 3; k++) {
             double x = 0.0;
             if (d.a != 0.0) x = d.a * G[k];
-            if (d.b != 0.0) x = x + d.b * R[k];
+            if (d.b != 0.0) x = fma(d.b, R[k], x);
             acc[k] = x;
         }
         for (int j = 0; j < d.nY; j++) {
             const double *y = vslot(c, V_Y0 + d.sY[j]) + off;
             const double cy = d.cY[j];
-            for (int k = 0; k < 3; k++) acc[k] = acc[k] + cy * y[k];
+            for (int k = 0; k < 3; k++) acc[k] = fma(cy, y[k], acc[k]);
         }
         for (int j = 0; j < d.nS; j++) {
             const double *s = vslot(c, V_S0 + d.sS[j]) + off;
             const double cs = d.cS[j];
-            for (int k = 0; k < 3; k++) acc[k] = acc[k] + cs * s[k];
+            for (int k = 0; k < 3; k++) acc[k] = fma(cs, s[k], acc[k]);
         }
         double dscale = 1.0;
         if (d.use_d) {
@@ -266,19 +272,19 @@ __global__ void __launch_bounds__(TI) k_dir(Ctx c) {
             R[k] = acc[k];
         }
         if (d.dots == 1) {
-            v[RD_RR] = acc[0] * acc[0] + acc[1] * acc[1] + acc[2] * acc[2];
-            v[RD_GR] = G[0] * acc[0] + G[1] * acc[1] + G[2] * acc[2];
+            v[RD_RR] = dot3_fma(acc, acc);
+            v[RD_GR] = dot3_fma(G, acc);
         } else if (d.dots == 2) {
 #pragma unroll
             for (int j = 0; j < NRING; j++) {
                 if (j < d.nY) {
                     const double *y = vslot(c, V_Y0 + d.sY[j]) + off;
-                    v[j] = y[0] * acc[0] + y[1] * acc[1] + y[2] * acc[2];
+                    v[j] = dot3_fma(y, acc);
                 }
             }
         }
     }
-    if (on) block_reduce_store_many(v, d.dots == 2 ? d.nY : 2, &c.red[(int64_t)blockIdx.x * NRED]);
+    if (on) block_reduce_columns<NRING>(v, d.dots == 2 ? d.nY : 2, 0u, &c.red[(int64_t)blockIdx.x * NRED]);
     if (c.sep_reduce || !last_block(&c.counters[WHICH == 0 ? CNT_DIR1 : CNT_DIR2])) return;
     last_block_systems<NRING>(
         c, 2, 0u, [](const SysState &S) { return S.dir[WHICH].on != 0; },
@@ -297,7 +303,7 @@ __global__ void __launch_bounds__(TI) k_sysreduce(Ctx c) {
     unsigned maxmask = 0u;
     if (STAGE == 0) {
         if (S.upd.op == U_NONE) return;
-        nv = S.upd.op == U_PUSH ? RU_N : 0;
+        nv = S.upd.op == U_PUSH ? ru_count(S.upd.nS) : 0;
     } else if (STAGE == 1 || STAGE == 2) {
         const DirOp &d = S.dir[STAGE - 1];
         if (!d.on) return;

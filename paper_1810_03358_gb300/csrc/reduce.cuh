@@ -47,18 +47,23 @@ __device__ inline bool last_block(unsigned int *cnt) {
     return am_last != 0;
 }
 
-// Block reduction of nv values (nv <= NRED) through shared memory: every
-// thread stores its values, then thread k sums column k over the block's
-// threads in order.  For many values this issues far fewer FP64 adds per
-// warp than shuffle trees (the FP64 pipe is the scarce one).
-__device__ inline void block_reduce_store_many(const double *v, int nv, double *dst) {
-    __shared__ double sh[NRED][TI + 1];
-    for (int k = 0; k < nv; k++) sh[k][threadIdx.x] = v[k];
+// Block reduction of nv <= NV values through shared memory: every thread
+// stores its values, then thread k sums (or, for the bits of maxmask, takes
+// the max of) column k over the block's threads in order.  One FP64
+// operation per thread and value, where a shuffle tree costs five: the FP64
+// pipe is the scarce unit of the kernels that use it.
+template <int NV>
+__device__ inline void block_reduce_columns(const double (&v)[NV], int nv, unsigned maxmask, double *dst) {
+    __shared__ double sh[NV][TI + 1];
+#pragma unroll
+    for (int k = 0; k < NV; k++)
+        if (k < nv) sh[k][threadIdx.x] = v[k];
     __syncthreads();
     if (threadIdx.x < nv) {
         const int k = threadIdx.x;
-        double x = 0.0;
-        for (int t = 0; t < TI; t++) x += sh[k][t];
+        const bool mx = (maxmask >> k) & 1u;
+        double x = sh[k][0];
+        for (int t = 1; t < TI; t++) x = mx ? fmax(x, sh[k][t]) : x + sh[k][t];
         dst[k] = x;
     }
 }

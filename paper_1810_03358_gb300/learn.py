@@ -135,6 +135,28 @@ def load_weights(path: str = WEIGHTS):
     return np.load(path) if os.path.exists(path) else None
 
 
+def evaluate(n_atoms=30000, seeds=(100000,), precision=ffmin.FFMIN_MIXED, max_iter=100000):
+    """Held-out comparison: each seed's n_atoms system minimized by plain
+    L-BFGS and by L-BFGS with the shipped network, one system at a time;
+    returns one dict per seed (iterations, evaluations, seconds, energies,
+    statuses of both runs)."""
+    w16 = load_weights()
+    if w16 is None:
+        raise RuntimeError(f"{WEIGHTS} is missing: train the network first (learn.main)")
+    out = []
+    for seed in seeds:
+        s = synth.make_system(n_atoms, seed)
+        row = {"seed": seed, "n_atoms": n_atoms}
+        for tag, use in (("plain", False), ("learned", True)):
+            res, sec, _ = minimize_with([s], w16, precision=precision, use=use, max_iter=max_iter)
+            r = res[0]
+            row[tag] = {"status": r["status_name"], "iterations": r["iterations"],
+                        "evals": r["energy_evals"] + r["grad_evals"], "seconds": sec,
+                        "energy": r["energy"], "grad_inf": r["grad_inf"]}
+        out.append(row)
+    return out
+
+
 def main(argv=None):
     """Train the shipped weights: plain MIXED L-BFGS trajectories of n_sys
     systems with 1,000-5,000 atoms (seeds 10000 + b), recorded every 20
@@ -145,7 +167,15 @@ def main(argv=None):
     ap.add_argument("--systems", type=int, default=256)
     ap.add_argument("--steps", type=int, default=1500)
     ap.add_argument("--out", default=WEIGHTS)
+    ap.add_argument("--evaluate", type=int, default=0, metavar="N_ATOMS",
+                    help="compare plain and learned L-BFGS on held-out systems of this size")
+    ap.add_argument("--seeds", default="100000")
     a = ap.parse_args(argv)
+    if a.evaluate:
+        import json
+        for row in evaluate(a.evaluate, [int(v) for v in a.seeds.split(",")]):
+            print(json.dumps(row), flush=True)
+        return
     t0 = time.time()
     systems = training_systems(n_sys=a.systems, seed0=10000, lo=1000, hi=5000)
     t1 = time.time()
