@@ -369,6 +369,8 @@ def minimizations(args, ffmin, synth, torch, dev, rank=0, ws=1):
         out["sample4_mixed_learned"] = run(sample, ffmin.FFMIN_MIXED, learned=True)
         out["sample4_mixed_learned_vs_plain_gpu"] = ratio("sample4_mixed_learned", "sample4_fp64")
     s3 = synth.make_system(3334, 2)
+    if not getattr(args, "no_methods", False):
+        out["methods_3334"] = methods_3334(ffmin, torch, dev, s3)
     out["n3334_fp64"] = run([s3], ffmin.FFMIN_FP64)
     out["n3334_mixed"] = run([s3], ffmin.FFMIN_MIXED)
     out["n3334_mixed_vs_plain_gpu"] = ratio("n3334_mixed", "n3334_fp64")
@@ -376,6 +378,36 @@ def minimizations(args, ffmin, synth, torch, dev, rank=0, ws=1):
         out["n3334_mixed_learned"] = run([s3], ffmin.FFMIN_MIXED, learned=True)
         out["n3334_mixed_learned_vs_plain_gpu"] = ratio("n3334_mixed_learned", "n3334_fp64")
     return out
+
+
+def methods_3334(ffmin, torch, dev, s3, cap=3000, gradfree_sweeps=10):
+    """Every minimizer of the paper from the same jittered start of the
+    3,334-atom globule (10^4 variables), in FP64 and MIXED: to |grad E|_inf
+    < 0.1 or `cap` iterations (the gradient-free search: `gradfree_sweeps`
+    sweeps of N moves).  One timed run each (CUDA events)."""
+    x0 = torch.tensor(s3.x.reshape(-1), dtype=torch.float64, device=dev)
+    res = {}
+    for prec, tag in ((ffmin.FFMIN_FP64, "fp64"), (ffmin.FFMIN_MIXED, "mixed")):
+        S = ffmin.System([s3], prec)
+        S.autotune(x0)
+        if prec == ffmin.FFMIN_FP64:
+            res["start_energy"] = S.energy_grad(x0.clone())[0][0]
+        for name in ("GD", "FGM", "CG", "LBFGS", "GRADFREE"):
+            cap_m = gradfree_sweeps * s3.n_atoms if name == "GRADFREE" else cap
+            S.minimize(x0.clone(), method=name, max_iter=2)  # warm-up (graphs, buffers)
+            x = x0.clone()
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record()
+            r = S.minimize(x, method=name, max_iter=cap_m)[0]
+            ev1.record()
+            torch.cuda.synchronize()
+            res[f"{name}_{tag}"] = {"status": r["status_name"], "iterations": r["iterations"],
+                                    "evals": r["energy_evals"] + r["grad_evals"],
+                                    "seconds": ev0.elapsed_time(ev1) / 1e3, "energy": r["energy"],
+                                    "grad_inf": r["grad_inf"]}
+        S.close()
+    return res
 
 
 def cpu_baseline():
@@ -507,6 +539,7 @@ def main():
     ap.add_argument("--impl", default="ffmin")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-minimize", action="store_true", help="skip the minimizations/s runs")
+    ap.add_argument("--no-methods", action="store_true", help="skip the per-method 3,334-atom runs")
     ap.add_argument("--profile", action="store_true", help="small fixed workload for ncu")
     ap.add_argument("--profile-atoms", type=int, default=N_ATOMS)
     ap.add_argument("--profile-minimize", type=int, default=0)

@@ -8,8 +8,11 @@ Two bars (FP64 path):
    must reproduce the oracle step for step: same iteration and evaluation
    counts, same stop reason, final energy within 1e-8 relative and the
    returned point within 1e-6 A.  The cap is 60 accepted steps: measured
-   differences grow about 1.14x per step from rounding level (1e-16) in the
-   fastest-diverging case (L-BFGS, 40 atoms), i.e. ~1e-12 at 60 steps.
+   differences grow about 1.14x per step from rounding level (1e-16) in
+   most cases, i.e. ~1e-12 at 60 steps.  Where the oracle's own capped run
+   is more sensitive (CG with LS_H on the 50-atom system moves by 3e-7 in
+   energy when its start moves by 1e-15 A), the energy and coordinate bars
+   become 10x that measured self-sensitivity.
 
 2. Full runs.  After a few hundred steps the two trajectories, equal up to
    rounding, separate (the landscape is rugged: measured agreement 1e-12 at
@@ -52,13 +55,36 @@ def run_gpu(ffmin, systems, prec, **opts):
     return xs, res, stats
 
 
+def oracle_sensitivity(oracle_mod, s, xo, ro, kw, members=3, eps=1e-15):
+    """How far the oracle's own capped run moves when its start moves by
+    eps A (rounding level): (max relative energy change, max coordinate
+    change, whether every member kept the oracle's counts)."""
+    de, dx, same = 0.0, 0.0, True
+    for k in range(1, members + 1):
+        x0 = s.x + eps * np.random.default_rng(k).normal(size=s.x.shape)
+        x1, r1 = oracle_mod.minimize(s, x0, **kw)
+        de = max(de, abs(r1["energy"] - ro["energy"]) / abs(ro["energy"]))
+        dx = max(dx, float(np.abs(x1 - xo).max()))
+        same = same and all(r1[k2] == ro[k2] for k2 in ("iterations", "energy_evals", "grad_evals"))
+    return de, dx, same
+
+
 def prefix_parity(oracle_mod, s, xg, rg, kw):
     xo, ro = oracle_mod.minimize(s, s.x, **kw)
     assert rg["status_name"] == STATUS[ro["status_name"]], (rg, ro)
     for k in ("iterations", "energy_evals", "grad_evals", "ls_failures"):
         assert rg[k] == ro[k], (k, rg, ro)
-    assert abs(rg["energy"] - ro["energy"]) <= 1e-8 * abs(ro["energy"]), (rg, ro)
-    assert np.abs(xg - xo).max() <= 1e-6
+    de = abs(rg["energy"] - ro["energy"]) / abs(ro["energy"])
+    dx = float(np.abs(xg - xo).max())
+    if de <= 1e-8 and dx <= 1e-6:
+        return
+    # some capped runs are chaotic already within the prefix: the oracle's
+    # own run, restarted 1e-15 A away, moves by a comparable amount.  The
+    # GPU run (different summation order, i.e. rounding-level differences in
+    # every evaluation) must then stay within 10x that self-sensitivity.
+    se, sx, _ = oracle_sensitivity(oracle_mod, s, xo, ro, kw)
+    assert de <= max(1e-8, 10.0 * se), (de, se, rg, ro)
+    assert dx <= max(1e-6, 10.0 * sx), (dx, sx)
 
 
 def ensemble_parity(oracle_mod, s, xg, rg, kw, members=4, eps=1e-12):
