@@ -16,7 +16,7 @@ from . import build as _build
 
 _lib = None
 
-GD, FGM, CG, LBFGS, GRADFREE = 0, 1, 2, 3, 4
+GD, FGM, CG, LBFGS, GRADFREE, OGM = 0, 1, 2, 3, 4, 5
 CG_PRP, CG_HS, CG_FR, CG_PRP_PLUS, CG_CD, CG_LS, CG_DY = range(7)
 LS_DEFAULT, LS_H, LS_PAR = 0, 1, 2
 STATUS = {0: "ok", 1: "nonfinite", 2: "linesearch", 3: "max_iter", 4: "bad_arg"}
@@ -46,7 +46,7 @@ class _Opt(C.Structure):
                 ("k_plus", C.c_double), ("k_minus", C.c_double), ("eps_h", C.c_double),
                 ("ls_par_K", C.c_int32), ("ls_par_g0", C.c_int32),
                 ("gradfree_delta", C.c_double), ("seed", C.c_uint64), ("precond_d", _dp),
-                ("mlp_w", _dp)]
+                ("mlp_w", _dp), ("ogm_step", C.c_double)]
 
 
 class _Res(C.Structure):

@@ -205,6 +205,64 @@ def test_fgm_theta_recurrence(oracle_mod):
     assert np.abs(xo - np.linalg.solve(A, b)).max() < 1e-4
 
 
+def test_ogm_first_step_is_cauchy_step(oracle_mod):
+    # with t_0 = 1 the first OGM step has y = x^0 and d = (1 + 1/t_1) grad f(x^0),
+    # i.e. steepest descent with an exact search (LS_PAR is exact on a
+    # quadratic): the Cauchy point x^0 - (g.g / g.Ag) g
+    A, b, _ = spd(10, 50.0, 3)
+    x0 = np.zeros(10)
+    g = A @ x0 - b
+    x1 = x0 - (g @ g) / (g @ A @ g) * g
+    xo, r = oracle_mod.minimize_fn(quad_fg(A, b), x0, method=oracle_mod.OGM, gtol_inf=1e-12,
+                                   max_iter=1)
+    assert r["iterations"] == 1
+    assert np.abs(xo - x1).max() < 1e-12 * (1 + np.abs(x1).max())
+
+
+@pytest.mark.parametrize("N", [1, 2, 7, 40])
+def test_ogm_fixed_step_equals_kim_fessler(oracle_mod, N):
+    # Eq. 11 with the fixed step 1/L is Drori and Teboulle's efficient form of
+    # the optimized gradient method; Kim and Fessler (Math. Prog. 2016) give
+    # the same iterates in momentum form:
+    #   y_{k+1} = x_k - grad f(x_k) / L,
+    #   x_{k+1} = y_{k+1} + (t_k - 1)/t_{k+1} (y_{k+1} - y_k)
+    #                     + t_k/t_{k+1} (y_{k+1} - x_k),   y_0 = x_0, t_0 = 1
+    A, b, lam = spd(12, 200.0, 5)
+    L = lam[-1]
+    x0 = np.random.default_rng(1).normal(size=12)
+    x, yp, t = x0.copy(), x0.copy(), 1.0
+    for _ in range(N):
+        y = x - (A @ x - b) / L
+        tn = 0.5 * (1.0 + np.sqrt(1.0 + 4.0 * t * t))
+        x = y + (t - 1.0) / tn * (y - yp) + t / tn * (y - x)
+        yp, t = y, tn
+    xo, r = oracle_mod.minimize_fn(quad_fg(A, b), x0, method=oracle_mod.OGM, gtol_inf=1e-14,
+                                   max_iter=N, ogm_step=1.0 / L)
+    assert r["iterations"] == N
+    assert np.abs(xo - x).max() <= 1e-11 * (1.0 + np.abs(x).max())
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_ogm_rate_on_convex_quadratics(oracle_mod, seed):
+    # Section 4, Eq. 12 (and the sentence after Eq. 13: the same bound holds
+    # with the step chosen by a line search): f(x^N) - f* <= L R^2 / N^2
+    n = 30
+    A, b, lam = spd(n, 1000.0, seed)
+    xs = np.linalg.solve(A, b)
+    fstar = 0.5 * xs @ A @ xs - b @ xs
+    x0 = np.zeros(n)
+    xo, r = oracle_mod.minimize_fn(quad_fg(A, b), x0, method=oracle_mod.OGM, gtol_inf=1e-7,
+                                   max_iter=1500)
+    f = oracle_mod.trace()["f"] - fstar
+    N = np.arange(1, len(f) + 1)
+    assert len(f) > 100
+    assert np.all(f <= lam[-1] * np.sum((x0 - xs) ** 2) / N ** 2 * (1 + 1e-9))
+    # t_{k+1} = (1 + sqrt(4 t_k^2 + 1)) / 2 from t_0 = 1
+    t = oracle_mod.trace()["theta"]
+    assert t[0] == pytest.approx((1 + np.sqrt(5.0)) / 2, rel=1e-15)
+    assert np.allclose(t[1:], (1 + np.sqrt(4 * t[:-1] ** 2 + 1)) / 2, rtol=1e-14)
+
+
 # ------------------------------ force field ------------------------------
 
 @pytest.mark.parametrize("method", ["GD", "FGM", "CG", "LBFGS"])
@@ -218,6 +276,20 @@ def test_force_field_minimizers_converge(oracle_mod, method):
     assert r["energy"] == pytest.approx(e1, rel=1e-12)
     assert np.abs(g1).max() == pytest.approx(r["grad_inf"], rel=1e-12)
     assert e1 < e0
+
+
+def test_force_field_ogm(oracle_mod):
+    # the literal OGM is slow on this non-convex landscape (Section 4's
+    # remark that CG-type methods win in practice) but must lower the
+    # energy and report the returned point
+    s = synth.make_system(40, 21)
+    e0 = oracle_mod.energy(s, s.x)
+    xo, r = oracle_mod.minimize(s, s.x, method=oracle_mod.OGM, max_iter=2000)
+    assert r["status_name"] in ("ok", "max_iter"), r
+    e1, g1 = oracle_mod.energy_grad(s, xo)
+    assert r["energy"] == pytest.approx(e1, rel=1e-12)
+    assert np.abs(g1).max() == pytest.approx(r["grad_inf"], rel=1e-12)
+    assert e1 < 1e-3 * e0
 
 
 def parab_brute_force(oracle_mod, s, x, moves, seed, delta):
