@@ -45,7 +45,15 @@ typedef enum {
     FFMIN_ERR_OOM = 7
 } ffmin_status;
 
-typedef enum { FFMIN_GD = 0, FFMIN_FGM = 1, FFMIN_CG = 2, FFMIN_LBFGS = 3, FFMIN_GRADFREE = 4 } ffmin_method;
+/* GD: adaptive steepest descent (Section 3, Eq. 4); FGM: Algorithm 1; CG:
+ * Algorithm 2; LBFGS: Algorithms 3-4; GRADFREE: random-atom parabolic moves
+ * (Section 3); OGM: the optimized gradient method of Section 4 (Eq. 11) with
+ * the step 1/L replaced by a line search from y (LS_PAR with G0 by default),
+ * the gradient evaluated at y and at every x^k, t_0 = 1, no momentum restart
+ * except after a failed line search. */
+typedef enum {
+    FFMIN_GD = 0, FFMIN_FGM = 1, FFMIN_CG = 2, FFMIN_LBFGS = 3, FFMIN_GRADFREE = 4, FFMIN_OGM = 5
+} ffmin_method;
 
 /* beta of CG (Section 5.1; Andrei 2008): d = previous unnormalised
  * direction, y = g+ - g.  PRP g+.y/|g|^2, HS g+.y/d.y, FR |g+|^2/|g|^2,

@@ -689,7 +689,7 @@ ffmin_status ffmin_energy_grad_host(ffmin_system *sys, const double *x_host, dou
 
 static ffmin_status check_options(ffmin_system *sys, const ffmin_options *o) {
     if (!o) return fail(sys, FFMIN_ERR_INVALID_ARG, "options is NULL");
-    if (o->method < FFMIN_GD || o->method > FFMIN_GRADFREE) return fail(sys, FFMIN_ERR_INVALID_ARG, "bad method");
+    if (o->method < FFMIN_GD || o->method > FFMIN_OGM) return fail(sys, FFMIN_ERR_INVALID_ARG, "bad method");
     if (o->cg_variant < 0 || o->cg_variant > FFMIN_CG_DY) return fail(sys, FFMIN_ERR_INVALID_ARG, "bad cg_variant");
     if (o->ls < 0 || o->ls > FFMIN_LS_PAR) return fail(sys, FFMIN_ERR_INVALID_ARG, "bad line search");
     if (o->method == FFMIN_LBFGS && (o->lbfgs_m < 1 || o->lbfgs_m > MAXM))

@@ -382,6 +382,25 @@ __device__ double cg_beta(int variant, double gpgp, double gpg, double gpd, doub
     }
 }
 
+// OGM (Section 4, Eq. 11): t_{k+1} = (1 + sqrt(4 t_k^2 + 1)) / 2
+__device__ __forceinline__ double ogm_tnext(double t) { return 0.5 * (1.0 + sqrt(4.0 * t * t + 1.0)); }
+
+// the update op of an OGM step: fold the accepted point (and the restart)
+// into X, G, X0 and the gradient sum DS, then form the next
+// y = (1 - 1/t') X + (1/t') X0 and r = -((1 - 1/t') G + (2/t') DS),
+// t' = t_{k+1} from S.ogm_t, and reduce <r, r>
+__device__ void ogm_step(SysState &S, int accept, int restart, double wds) {
+    const double tn = ogm_tnext(S.ogm_t);
+    S.upd.op = U_OGM;
+    S.upd.accept = accept;
+    S.upd.restart = restart;
+    S.upd.h = wds;
+    S.upd.a = 1.0 - 1.0 / tn;
+    S.upd.b = 1.0 / tn;
+    S.upd.inv = 2.0 / tn;
+    S.phase = PH_OGM_UPD;
+}
+
 // reductions of the finalize kernel
 enum { RF_E = 0, RF_GG, RF_GINF, RF_GTG, RF_GTR, RF_BAD, RF_EPAIR, RF_N };
 
@@ -439,16 +458,43 @@ __device__ void on_eval_done(const Ctx &c, SysState &S, const double *v) {
             finish(c, S, FFMIN_OK, S.f, S.ginf);
             return;
         }
+        if (S.method == FFMIN_OGM) {  // x^0 = X, t_0 = 1, DS = grad f(x^0)
+            if (cap_hit(S)) {
+                finish(c, S, FFMIN_ERR_MAX_ITER, S.f, S.ginf);
+                return;
+            }
+            S.ogm_t = 1.0;
+            ogm_step(S, 1, 1, 0.0);
+            return;
+        }
         set_dir(S, 1, -1.0, 0.0, 1.0, 1);
         S.phase = PH_DIR;
+        return;
+    }
+
+    const bool ogm = S.method == FFMIN_OGM;
+    if (S.phase == PH_OGM_Y) {  // E and grad at y: the base of the line search
+        if (bad) {
+            finish(c, S, FFMIN_ERR_NONFINITE, S.f, S.ginf);
+            return;
+        }
+        S.fstar = E;
+        S.epair_base = S.epair_last;
+        S.slope = v[RF_GTR] / S.rnorm;
+        S.rg = v[RF_GTR];
+        S.ls_kind = S.ls == FFMIN_LS_DEFAULT ? FFMIN_LS_PAR : S.ls;
+        const double h = ls_start(S, S.h0);
+        set_eval(S, EV_E, V_W, V_R, h, 1.0 / S.rnorm);
+        S.phase = PH_LS;
         return;
     }
 
     if (S.phase == PH_LS) {
         const double f = bad ? HUGE_VAL : finite_or_inf(E);
         LsOut o = ls_feed(S, f);
+        const int lsb = (fgm || ogm) ? V_W : V_X;  // base point of the search
         if (!o.done) {
-            set_eval(S, EV_E, fgm ? V_W : V_X, V_R, o.h, S.ev_scale);
+            set_eval(S, EV_E, lsb, V_R, o.h, S.ev_scale);
             return;
         }
         if (o.h != 0.0) {
@@ -458,7 +504,7 @@ __device__ void on_eval_done(const Ctx &c, SysState &S, const double *v) {
                 return;
             }
             S.h_acc = o.h;
-            set_eval(S, EV_EG, V_X, V_R, o.h, S.ev_scale);
+            set_eval(S, EV_EG, lsb, V_R, o.h, S.ev_scale);
             S.phase = PH_ACCEPT;
             return;
         }
@@ -475,6 +521,15 @@ __device__ void on_eval_done(const Ctx &c, SysState &S, const double *v) {
             S.upd.op = U_FGM_RESET;
             S.fx = S.fw;
             fgm_next_w(S);
+            return;
+        }
+        if (ogm) {  // restart from x^k: x^0 = X, t = 1, DS = G
+            if (cap_hit(S)) {
+                finish(c, S, FFMIN_ERR_MAX_ITER, S.f, S.ginf);
+                return;
+            }
+            S.ogm_t = 1.0;
+            ogm_step(S, 0, 1, 0.0);
             return;
         }
         S.ring_count = 0;
@@ -506,6 +561,20 @@ __device__ void on_eval_done(const Ctx &c, SysState &S, const double *v) {
         S.iter++;
         S.h0 = fabs(S.h_acc);
         const double gninf = v[RF_GINF];
+        if (ogm) {  // x^{k+1} accepted: t = t_{k+1}, DS += t_{k+1} grad f(x^{k+1})
+            const double tn = ogm_tnext(S.ogm_t);
+            S.ogm_t = tn;
+            S.f = E;
+            S.ginf = gninf;
+            S.gg = v[RF_GG];
+            ogm_step(S, 1, 0, tn);
+            if (S.ginf < S.gtol || mixed_handover(S, E, gninf)) {
+                finish(c, S, FFMIN_OK, S.f, S.ginf);
+                return;
+            }
+            if (cap_hit(S)) finish(c, S, FFMIN_ERR_MAX_ITER, S.f, S.ginf);
+            return;
+        }
         if (S.method == FFMIN_LBFGS) {
             // stage (s, y) and the inner products with the committed pairs
             int used[NRING];
@@ -578,6 +647,13 @@ __device__ void on_update_done(const Ctx &c, SysState &S, const double *v) {
     S.upd.best = 0;
     if (S.phase == PH_DONE) {
         deactivate(c, S);
+        return;
+    }
+    if (op == U_OGM) {  // <r, r> of the new direction: evaluate E and grad at y
+        if (S.phase != PH_OGM_UPD) return;
+        S.rnorm = sqrt(v[0]);
+        set_eval(S, EV_EG, V_W, -1, 0.0, 1.0);
+        S.phase = PH_OGM_Y;
         return;
     }
     if (op != U_PUSH) return;

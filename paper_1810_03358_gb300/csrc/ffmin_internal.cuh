@@ -30,7 +30,7 @@ constexpr int NRING = MAXM + 1;  // ring slots (m committed pairs + one staging 
 constexpr int NRED = 2 * NRING + 4;  // reduction values per tile
 
 enum Slot : int {
-    V_X = 0, V_G, V_R, V_XT, V_GT, V_W, V_P, V_XB, V_D, V_XIN,
+    V_X = 0, V_G, V_R, V_XT, V_GT, V_W, V_P, V_XB, V_D, V_XIN, V_X0, V_DS,
     V_S0, V_Y0 = V_S0 + NRING, V_NSLOT = V_Y0 + NRING
 };
 
@@ -43,11 +43,14 @@ enum UpdKind : int {
     U_FGM_W,         // W <- XT, G <- GT (optionally XB <- XT)
     U_FGM_ACCEPT,    // Xn = fma(h, R * inv, W); P <- Xn - X (0 on restart); X <- Xn (XB <- Xn)
     U_FGM_RESET,     // X <- W, P <- 0
-    U_FGM_BEST_W     // XB <- W
+    U_FGM_BEST_W,    // XB <- W
+    U_OGM            // OGM: (accept) X <- XT, G <- GT; (restart) X0 <- X, DS <- G, else
+                     // (accept) DS += h G; then W = a X + b X0, R = -(a G + inv DS), <R, R>
 };
 
 enum Phase : int {
-    PH_IDLE = 0, PH_START, PH_DIR, PH_LS, PH_ACCEPT, PH_FGM_W, PH_FINAL, PH_EVAL_ONLY, PH_DONE
+    PH_IDLE = 0, PH_START, PH_DIR, PH_LS, PH_ACCEPT, PH_FGM_W, PH_FINAL, PH_EVAL_ONLY, PH_DONE,
+    PH_OGM_UPD, PH_OGM_Y
 };
 
 // a pair item (i-tile, j-chunk); tile < 0 marks a bonded item whose j0, nj
@@ -68,7 +71,8 @@ struct DirOp {
 struct UpdOp {
     int32_t op, best, restart, stage;  // stage: physical ring slot for U_PUSH
     int32_t nS, sS[NRING];             // committed s slots (U_PUSH dots)
-    double h, inv;
+    int32_t accept;                    // U_OGM: the step to XT was accepted
+    double h, inv, a, b;
 };
 
 struct SysState {
@@ -103,6 +107,7 @@ struct SysState {
     double alpha[NRING];
     // FGM
     double th_prev, fx, fb, fw, xb_ginf;
+    double ogm_t;  // OGM: t_k
     int32_t xb_known, result_slot;
     // result
     double res_f, res_ginf;

@@ -176,6 +176,36 @@ __global__ void __launch_bounds__(TI) k_update(Ctx c) {
             for (int k = 0; k < 3; k++) { X[k] = XT[k]; G[k] = GT[k]; }
         }
         block_reduce_columns<RU_N>(v, ru_count(S.upd.nS), 0u, &c.red[(int64_t)blockIdx.x * NRED]);
+    } else if (op == U_OGM) {
+        double v[1] = {0.0};
+        if (i < t.na) {
+            const int64_t off = 3 * (int64_t)(t.a0 + i);
+            double *X = vslot(c, V_X) + off, *G = vslot(c, V_G) + off, *W = vslot(c, V_W) + off;
+            double *R = vslot(c, V_R) + off, *X0 = vslot(c, V_X0) + off, *DS = vslot(c, V_DS) + off;
+            const double *XT = vslot(c, V_XT) + off, *GT = vslot(c, V_GT) + off;
+            const UpdOp &u = S.upd;
+            double rr[3];
+            for (int k = 0; k < 3; k++) {
+                double x = X[k], g = G[k];
+                if (u.accept) { x = XT[k]; g = GT[k]; X[k] = x; G[k] = g; }
+                double x0, ds;
+                if (u.restart) {
+                    x0 = x;
+                    ds = g;
+                    X0[k] = x0;
+                } else {
+                    x0 = X0[k];
+                    ds = u.accept ? fma(u.h, g, DS[k]) : DS[k];
+                }
+                DS[k] = ds;
+                W[k] = fma(u.a, x, u.b * x0);
+                const double r = -fma(u.a, g, u.inv * ds);
+                R[k] = r;
+                rr[k] = r;
+            }
+            v[0] = dot3_fma(rr, rr);
+        }
+        block_reduce_columns<1>(v, 1, 0u, &c.red[(int64_t)blockIdx.x * NRED]);
     } else if (op != U_NONE && i < t.na) {
         const int64_t off = 3 * (int64_t)(t.a0 + i);
         double *X = vslot(c, V_X) + off, *G = vslot(c, V_G) + off, *W = vslot(c, V_W) + off;
@@ -216,7 +246,7 @@ __global__ void __launch_bounds__(TI) k_update(Ctx c) {
     last_block_systems<RU_N>(
         c, RU_N, 0u, [](const SysState &S) { return S.upd.op != U_NONE; },
         [&](SysState &S, const double *tot) { on_update_done(c, S, tot); },
-        [](const SysState &S) { return S.upd.op == U_PUSH ? ru_count(S.upd.nS) : 0; });
+        [](const SysState &S) { return S.upd.op == U_PUSH ? ru_count(S.upd.nS) : (S.upd.op == U_OGM ? 1 : 0); });
     __syncthreads();
     if (threadIdx.x == 0) c.counters[CNT_UPD] = 0;
 }
@@ -303,7 +333,7 @@ __global__ void __launch_bounds__(TI) k_sysreduce(Ctx c) {
     unsigned maxmask = 0u;
     if (STAGE == 0) {
         if (S.upd.op == U_NONE) return;
-        nv = S.upd.op == U_PUSH ? ru_count(S.upd.nS) : 0;
+        nv = S.upd.op == U_PUSH ? ru_count(S.upd.nS) : (S.upd.op == U_OGM ? 1 : 0);
     } else if (STAGE == 1 || STAGE == 2) {
         const DirOp &d = S.dir[STAGE - 1];
         if (!d.on) return;

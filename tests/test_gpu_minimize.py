@@ -123,7 +123,7 @@ def ensemble_parity(oracle_mod, s, xg, rg, kw, members=4, eps=1e-12):
     return energies
 
 
-@pytest.mark.parametrize("method", [0, 1, 2, 3])
+@pytest.mark.parametrize("method", [0, 1, 2, 3, 5])
 @pytest.mark.parametrize("n,seed", [(40, 21), (130, 22)])
 def test_prefix_methods(ff, oracle_mod, method, n, seed):
     s = synth.make_system(n, seed)
@@ -141,7 +141,7 @@ def test_prefix_cg_variants(ff, oracle_mod, variant):
 
 
 @pytest.mark.parametrize("ls", [1, 2])
-@pytest.mark.parametrize("method", [0, 1, 2, 3])
+@pytest.mark.parametrize("method", [0, 1, 2, 3, 5])
 def test_prefix_line_search_choice(ff, oracle_mod, ls, method):
     s = synth.make_system(50, 24)
     kw = dict(method=method, ls=ls, max_iter=PREFIX)
@@ -168,6 +168,38 @@ def test_prefix_batched(ff, oracle_mod):
         prefix_parity(oracle_mod, s, xg[b], rg[b], kw)
 
 
+def test_prefix_ogm_batched_and_options(ff, oracle_mod):
+    # OGM (Section 4, Eq. 11 with a line search): a batch, each system against
+    # its own oracle run; and the G0-free search variant
+    systems = [synth.make_system(n, 330 + k) for k, n in enumerate([60, 33, 7])]
+    kw = dict(method=5, max_iter=PREFIX)
+    xg, rg, _ = run_gpu(ff, systems, 0, **kw)
+    for b, s in enumerate(systems):
+        prefix_parity(oracle_mod, s, xg[b], rg[b], kw)
+    kw = dict(method=5, max_iter=PREFIX, ls_par_g0=0)
+    xg, rg, _ = run_gpu(ff, systems[:1], 0, **kw)
+    prefix_parity(oracle_mod, systems[0], xg[0], rg[0], kw)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_ogm_long_capped_run(ff, oracle_mod, prec):
+    # beyond the prefix the trajectories separate; the run must lower the
+    # energy and report the energy of the point it returns (MIXED: from the
+    # FP32 pair terms, as the cap ends the FP32 phase)
+    s = synth.make_system(150, 31)
+    xg, rg, _ = run_gpu(ff, [s], prec, method=5, max_iter=600)
+    r = rg[0]
+    assert r["status_name"] in ("ok", "max_iter"), r
+    e0 = oracle_mod.energy(s, s.x)
+    e1, g1 = oracle_mod.energy_grad(s, xg[0])
+    assert e1 < 1e-3 * e0
+    if prec == 0:
+        assert abs(e1 - r["energy"]) <= 1e-9 * abs(e1), (e1, r)
+    else:  # the energy bar of the FP32 pair terms, relative to sum |terms|
+        terms = oracle_mod.energy_terms(s, xg[0])[0]
+        assert abs(e1 - r["energy"]) <= 1e-5 * terms["sum_abs"], (e1, r)
+
+
 def test_evaluation_cap(ff, oracle_mod):
     s = synth.make_system(30, 29)
     kw = dict(method=3, max_evals=57)
@@ -180,7 +212,7 @@ def test_already_converged_start(ff, oracle_mod):
     s = synth.make_system(25, 30)
     xo, ro = oracle_mod.minimize(s, s.x, method=3)
     s.x = xo
-    for m in (0, 1, 2, 3):
+    for m in (0, 1, 2, 3, 5):
         xg, rg, _ = run_gpu(ff, [s], 0, method=m)
         assert rg[0]["status_name"] == "ok" and rg[0]["iterations"] == 0 and rg[0]["grad_evals"] == 1
 
