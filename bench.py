@@ -392,7 +392,7 @@ def methods_3334(ffmin, torch, dev, s3, cap=3000, gradfree_sweeps=10):
         S.autotune(x0)
         if prec == ffmin.FFMIN_FP64:
             res["start_energy"] = S.energy_grad(x0.clone())[0][0]
-        for name in ("GD", "FGM", "CG", "LBFGS", "GRADFREE"):
+        for name in ("GD", "FGM", "CG", "LBFGS", "OGM", "GRADFREE"):
             cap_m = gradfree_sweeps * s3.n_atoms if name == "GRADFREE" else cap
             S.minimize(x0.clone(), method=name, max_iter=2)  # warm-up (graphs, buffers)
             x = x0.clone()
