@@ -37,6 +37,11 @@ typedef struct {
     const int32_t *dihedral_idx;                     /* [nd*4] */
     const double *dihedral_v;                        /* [nd*4] V1..V4 */
     double coulomb_c;
+    /* 0: every pair interacts (Section 2).  1: a force-field variant (not in
+     * the paper): pairs joined by a bond or by the ends of an angle are
+     * excluded, the end atoms of a dihedral interact scaled by scale14. */
+    int32_t exclusions;
+    double scale14;
 } orc_ff;
 
 /* Energy split by term plus the sum of |term| over every term and pair. */

@@ -11,13 +11,17 @@
  *   E_vdw     = 4 sum_{i<j} sqrt(eps_i eps_j) [(s/r)^12 - (s/r)^6],
  *               s = sqrt(sigma_i sigma_j)
  * Pairs run over ALL i < j: the paper's non-bonded forces act regardless of
- * whether a bond joins the atoms, so there is no exclusion list.
+ * whether a bond joins the atoms, so there is no exclusion list.  With
+ * ff->exclusions (a force-field variant outside the paper) each pair term is
+ * multiplied by s_ij: 0 for atoms joined by a bond or the ends of an angle,
+ * scale14 for the ends of a dihedral (when not excluded), else 1.
  * Gradients are the explicit formulas (Section 2 prefers them to autodiff).
  */
 #include "ffmin_oracle.h"
 
 #include <math.h>
 #include <stddef.h>
+#include <stdlib.h>
 
 static void sub3(const double *a, const double *b, double *o) {
     o[0] = a[0] - b[0]; o[1] = a[1] - b[1]; o[2] = a[2] - b[2];
@@ -29,6 +33,60 @@ static void cross3(const double *a, const double *b, double *o) {
     o[0] = a[1] * b[2] - a[2] * b[1];
     o[1] = a[2] * b[0] - a[0] * b[2];
     o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+/* ---- the scale s_ij of the pair (i, j) ---- */
+typedef struct {
+    int64_t key; /* min(i,j) * N + max(i,j) */
+    double s;
+} pscale_t;
+
+static int cmp_pscale(const void *a, const void *b) {
+    const pscale_t *x = (const pscale_t *)a, *y = (const pscale_t *)b;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    return x->s < y->s ? -1 : (x->s > y->s ? 1 : 0);
+}
+
+static int64_t pkey(const orc_ff *ff, int32_t i, int32_t j) {
+    return i < j ? (int64_t)i * ff->n_atoms + j : (int64_t)j * ff->n_atoms + i;
+}
+
+/* Sorted table of the scaled pairs (smallest scale first among duplicates),
+ * or NULL when every pair has scale 1.  *m = entries. */
+static pscale_t *scale_table(const orc_ff *ff, int32_t *m) {
+    *m = 0;
+    if (!ff->exclusions) return NULL;
+    int32_t cap = ff->n_bonds + ff->n_angles + ff->n_dihedrals;
+    pscale_t *t = (pscale_t *)malloc(sizeof(pscale_t) * (size_t)(cap > 0 ? cap : 1));
+    int32_t k = 0;
+    for (int32_t b = 0; b < ff->n_bonds; b++) {
+        t[k].key = pkey(ff, ff->bond_idx[2 * b], ff->bond_idx[2 * b + 1]);
+        t[k++].s = 0.0;
+    }
+    for (int32_t b = 0; b < ff->n_angles; b++) {
+        t[k].key = pkey(ff, ff->angle_idx[3 * b], ff->angle_idx[3 * b + 2]);
+        t[k++].s = 0.0;
+    }
+    for (int32_t b = 0; b < ff->n_dihedrals; b++) {
+        t[k].key = pkey(ff, ff->dihedral_idx[4 * b], ff->dihedral_idx[4 * b + 3]);
+        t[k++].s = ff->scale14;
+    }
+    qsort(t, (size_t)k, sizeof(pscale_t), cmp_pscale);
+    *m = k;
+    return t;
+}
+
+/* s_ij: the first (smallest) entry of the pair's key, else 1 */
+static double pair_scale(const orc_ff *ff, const pscale_t *t, int32_t m, int32_t i, int32_t j) {
+    if (!t) return 1.0;
+    const int64_t key = pkey(ff, i, j);
+    int32_t lo = 0, hi = m;
+    while (lo < hi) {
+        int32_t mid = (lo + hi) / 2;
+        if (t[mid].key < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return (lo < m && t[lo].key == key) ? t[lo].s : 1.0;
 }
 
 /* Pair term between atoms with the given parameters at separation vector
@@ -155,15 +213,22 @@ int orc_energy_terms(const orc_ff *ff, const double *x, double *grad, orc_terms 
     if (grad)
         for (int k = 0; k < 3 * n; k++) grad[k] = 0.0;
 
-    /* non-bonded: every unordered pair i < j */
+    /* non-bonded: every unordered pair i < j, times its scale s_ij */
+    int32_t m_sc;
+    pscale_t *sc = scale_table(ff, &m_sc);
     for (int i = 0; i < n; i++) {
         for (int j = i + 1; j < n; j++) {
             double d[3];
             sub3(x + 3 * i, x + 3 * j, d);
             if (dot3(d, d) == 0.0) { status = ORC_NONFINITE; continue; }
+            const double s = pair_scale(ff, sc, m_sc, i, j);
+            if (s == 0.0) continue;
             double ec, ev, f;
             pair_term(ff->coulomb_c, ff->charge[i], ff->charge[j], ff->sigma[i], ff->sigma[j],
                       ff->epsilon[i], ff->epsilon[j], d, &ec, &ev, &f);
+            ec *= s;
+            ev *= s;
+            f *= s;
             t.coulomb += ec;
             t.vdw += ev;
             t.sum_abs += fabs(ec) + fabs(ev);
@@ -175,6 +240,7 @@ int orc_energy_terms(const orc_ff *ff, const double *x, double *grad, orc_terms 
             }
         }
     }
+    free(sc);
     /* bonds */
     for (int b = 0; b < ff->n_bonds; b++) {
         int i = ff->bond_idx[2 * b], j = ff->bond_idx[2 * b + 1];
@@ -228,13 +294,18 @@ int orc_energy_terms(const orc_ff *ff, const double *x, double *grad, orc_terms 
 double orc_row_energy(const orc_ff *ff, const double *x, int32_t i, const double p[3]) {
     const int n = ff->n_atoms;
     double e = 0.0;
+    int32_t m_sc;
+    pscale_t *sc = scale_table(ff, &m_sc);
     for (int j = 0; j < n; j++) {
         if (j == i) continue;
+        const double s = pair_scale(ff, sc, m_sc, i, j);
+        if (s == 0.0) continue;
         double d[3], ec, ev, f;
         sub3(p, x + 3 * j, d);
-        e += pair_term(ff->coulomb_c, ff->charge[i], ff->charge[j], ff->sigma[i], ff->sigma[j],
-                       ff->epsilon[i], ff->epsilon[j], d, &ec, &ev, &f);
+        e += s * pair_term(ff->coulomb_c, ff->charge[i], ff->charge[j], ff->sigma[i], ff->sigma[j],
+                           ff->epsilon[i], ff->epsilon[j], d, &ec, &ev, &f);
     }
+    free(sc);
 #define POS(a) ((a) == i ? p : x + 3 * (a))
     for (int b = 0; b < ff->n_bonds; b++) {
         int a0 = ff->bond_idx[2 * b], a1 = ff->bond_idx[2 * b + 1];
@@ -273,15 +344,20 @@ int32_t orc_neighbour_count(const orc_ff *ff, const double *x, int32_t i, double
 int orc_atom_gradient(const orc_ff *ff, const double *x, int32_t i, double *g3) {
     int status = ORC_OK;
     g3[0] = g3[1] = g3[2] = 0.0;
+    int32_t m_sc;
+    pscale_t *sc = scale_table(ff, &m_sc);
     for (int j = 0; j < ff->n_atoms; j++) {
         if (j == i) continue;
         double d[3], ec, ev, f;
         sub3(x + 3 * i, x + 3 * j, d);
         if (dot3(d, d) == 0.0) { status = ORC_NONFINITE; continue; }
+        const double s = pair_scale(ff, sc, m_sc, i, j);
+        if (s == 0.0) continue;
         pair_term(ff->coulomb_c, ff->charge[i], ff->charge[j], ff->sigma[i], ff->sigma[j],
                   ff->epsilon[i], ff->epsilon[j], d, &ec, &ev, &f);
-        for (int a = 0; a < 3; a++) g3[a] += f * d[a];
+        for (int a = 0; a < 3; a++) g3[a] += s * f * d[a];
     }
+    free(sc);
     for (int b = 0; b < ff->n_bonds; b++) {
         const int32_t *q = ff->bond_idx + 2 * b;
         if (q[0] != i && q[1] != i) continue;

@@ -30,7 +30,8 @@ class _FF(C.Structure):
                 ("n_bonds", C.c_int32), ("bond_idx", _ip), ("bond_k", _dp), ("bond_r0", _dp),
                 ("n_angles", C.c_int32), ("angle_idx", _ip), ("angle_k", _dp),
                 ("angle_theta0", _dp), ("n_dihedrals", C.c_int32), ("dihedral_idx", _ip),
-                ("dihedral_v", _dp), ("coulomb_c", C.c_double)]
+                ("dihedral_v", _dp), ("coulomb_c", C.c_double), ("exclusions", C.c_int32),
+                ("scale14", C.c_double)]
 
 
 class _Terms(C.Structure):
@@ -123,7 +124,8 @@ class FF:
                      k["angle_idx"].ctypes.data_as(_ip), _dptr(k["angle_k"]),
                      _dptr(k["angle_theta0"]), int(k["dihedral_v"].shape[0] // 4),
                      k["dihedral_idx"].ctypes.data_as(_ip), _dptr(k["dihedral_v"]),
-                     float(s.coulomb_c))
+                     float(s.coulomb_c), int(getattr(s, "exclusions", 0)),
+                     float(getattr(s, "scale14", 0.5)))
 
 
 def _ff(s):

@@ -52,6 +52,10 @@ class System:
     dihedral_idx: np.ndarray  # [nd, 4] int32
     dihedral_v: np.ndarray   # [nd, 4] V1..V4
     coulomb_c: float = COULOMB_KCAL
+    # 0: every pair interacts (the paper); 1: bonded and angle-end pairs
+    # excluded, dihedral-end pairs scaled by scale14 (force-field variant)
+    exclusions: int = 0
+    scale14: float = 0.5
     seed: int = 0
     meta: dict = field(default_factory=dict)
 
