@@ -86,6 +86,13 @@ typedef struct {
     const int32_t *dihedral_idx;                       /* [nd*4] */
     const double *dihedral_v;                          /* [nd*4] V1..V4 */
     double coulomb_c;  /* 0 -> 332.0716 kcal*A/(mol*e^2) = 1389.38757 / 4.184 (Section 2) */
+    /* 0: every pair interacts (Section 2).  1: a force-field variant, not in
+     * the paper: pairs joined by a bond or by the ends of an angle are
+     * excluded, the end atoms of a dihedral interact scaled by scale14
+     * (finite, >= 0).  Evaluated as FP64 correction terms (weight s - 1 on
+     * the pair term) beside the all-pairs sweep. */
+    int32_t exclusions;
+    double scale14;
 } ffmin_topology;
 
 typedef struct {

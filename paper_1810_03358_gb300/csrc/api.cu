@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <map>
 #include <vector>
 
 #include "ffmin_internal.cuh"
@@ -66,8 +67,8 @@ struct ffmin_system {
     Tile *d_tiles = nullptr;
     Item *d_items = nullptr;
     int2 *d_sys_items = nullptr;
-    std::vector<int32_t> term_off[3];  // per-system offsets of bonds, angles, dihedrals
-    int nb_total = 0, na_total = 0;
+    std::vector<int32_t> term_off[4];  // per-system offsets of bonds, angles, dihedrals, corrections
+    int nb_total = 0, na_total = 0, nd_total = 0;
 };
 
 // j-chunk length of a system: a multiple of TJ, chosen so that the whole
@@ -97,13 +98,14 @@ static void build_items(ffmin_system *sys, int density, std::vector<Item> &items
     size_t t = 0;
     for (int b = 0; b < sys->n_sys; b++) {
         const int first = (int)items.size();
-        // bonded ranges of system b: bonds, angles, dihedrals (global indices)
-        const int starts[3] = {sys->term_off[0][b], sys->nb_total + sys->term_off[1][b],
-                               sys->nb_total + sys->na_total + sys->term_off[2][b]};
-        const int counts[3] = {sys->term_off[0][b + 1] - sys->term_off[0][b],
-                               sys->term_off[1][b + 1] - sys->term_off[1][b],
-                               sys->term_off[2][b + 1] - sys->term_off[2][b]};
-        for (int ty = 0; ty < 3; ty++) {
+        // bonded ranges of system b: bonds, angles, dihedrals, exclusion
+        // corrections (global indices)
+        const int starts[4] = {sys->term_off[0][b], sys->nb_total + sys->term_off[1][b],
+                               sys->nb_total + sys->na_total + sys->term_off[2][b],
+                               sys->nb_total + sys->na_total + sys->nd_total + sys->term_off[3][b]};
+        int counts[4];
+        for (int ty = 0; ty < 4; ty++) counts[ty] = sys->term_off[ty][b + 1] - sys->term_off[ty][b];
+        for (int ty = 0; ty < 4; ty++) {
             for (int k = 0; k < counts[ty]; k += BONDED_ITEM_TERMS) {
                 Item it{};
                 it.tile = -1;
@@ -282,6 +284,9 @@ ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t pre
         for (int a = 0; a < t.n_atoms; a++)
             if (!(t.sigma[a] >= 0.0) || !(t.epsilon[a] >= 0.0) || !std::isfinite(t.charge[a]))
                 return fail(nullptr, FFMIN_ERR_INVALID_ARG, "sigma/epsilon must be >= 0 and charges finite");
+        if ((t.exclusions != 0 && t.exclusions != 1) ||
+            (t.exclusions && !(t.scale14 >= 0.0 && std::isfinite(t.scale14))))
+            return fail(nullptr, FFMIN_ERR_INVALID_ARG, "exclusions must be 0 or 1, scale14 finite and >= 0");
         total += t.n_atoms;
     }
     if (total > (1LL << 30)) return fail(nullptr, FFMIN_ERR_INVALID_ARG, "too many atoms");
@@ -318,6 +323,9 @@ ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t pre
     std::vector<double2> bpar, apar;
     std::vector<int4> aidx, didx;
     std::vector<double4_32a> dpar;
+    std::vector<int2> xidx;          // exclusion corrections: atom pairs
+    std::vector<double> xw;          // and weights s_ij - 1
+    std::vector<int32_t> xcount(n_sys, 0);
     std::vector<std::vector<int2>> inc_lists(total);
     for (int b = 0; b < n_sys; b++) {
         const ffmin_topology &t = tops[b];
@@ -359,6 +367,34 @@ ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t pre
             dpar.push_back(make_double4_32a(v[0], v[1], v[2], v[3]));
             for (int p = 0; p < 4; p++) inc_lists[A + q[p]].push_back(make_int2((2 << 2) | p, term));
         }
+        if (t.exclusions) {
+            // s_ij = 0 for bonded and angle-end pairs, scale14 for dihedral
+            // ends (the smallest scale wins for a pair listed twice); one
+            // correction term of weight s_ij - 1 per pair with s_ij != 1,
+            // in ascending pair order
+            std::map<int64_t, double> scale;
+            auto add = [&](int i, int j, double s) {
+                const int64_t key = (int64_t)std::min(i, j) * t.n_atoms + std::max(i, j);
+                auto it = scale.find(key);
+                if (it == scale.end()) scale[key] = s;
+                else it->second = std::min(it->second, s);
+            };
+            for (int k = 0; k < t.n_bonds; k++) add(t.bond_idx[2 * k], t.bond_idx[2 * k + 1], 0.0);
+            for (int k = 0; k < t.n_angles; k++) add(t.angle_idx[3 * k], t.angle_idx[3 * k + 2], 0.0);
+            for (int k = 0; k < t.n_dihedrals; k++)
+                add(t.dihedral_idx[4 * k], t.dihedral_idx[4 * k + 3], t.scale14);
+            for (const auto &kv : scale) {
+                const double w = kv.second - 1.0;
+                const int i = (int)(kv.first / t.n_atoms), j = (int)(kv.first % t.n_atoms);
+                if (w == 0.0 || i == j) continue;
+                const int term = (int)xidx.size();
+                xidx.push_back(make_int2((int)(A + i), (int)(A + j)));
+                xw.push_back(w);
+                inc_lists[A + i].push_back(make_int2((3 << 2) | 0, term));
+                inc_lists[A + j].push_back(make_int2((3 << 2) | 1, term));
+                xcount[b]++;
+            }
+        }
         // tiles of 128 atoms (never straddling systems)
         tile0[b] = (int)tiles.size();
         for (int a0 = 0; a0 < t.n_atoms; a0 += TI) {
@@ -372,24 +408,27 @@ ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t pre
     }
     // bonded work items go first in the queue: they are latency-bound FP64
     // work and overlap with the FP32 pair items that follow
-    const int n_terms = (int)(bidx.size() + aidx.size() + didx.size());
+    const int n_terms = (int)(bidx.size() + aidx.size() + didx.size() + xidx.size());
     std::vector<int32_t> term_sys(std::max(n_terms, 1), 0);
     {
         int t = 0;
         for (int b = 0; b < n_sys; b++) for (int k = 0; k < tops[b].n_bonds; k++) (void)k, term_sys[t++] = b;
         for (int b = 0; b < n_sys; b++) for (int k = 0; k < tops[b].n_angles; k++) (void)k, term_sys[t++] = b;
         for (int b = 0; b < n_sys; b++) for (int k = 0; k < tops[b].n_dihedrals; k++) (void)k, term_sys[t++] = b;
+        for (int b = 0; b < n_sys; b++) for (int k = 0; k < xcount[b]; k++) (void)k, term_sys[t++] = b;
     }
     sys->n_terms = n_terms;
     sys->n_bitems = (n_terms + BONDED_ITEM_TERMS - 1) / BONDED_ITEM_TERMS;
     sys->tiles_h = tiles;
     sys->nb_total = (int)bidx.size();
     sys->na_total = (int)aidx.size();
-    for (int ty = 0; ty < 3; ty++) sys->term_off[ty].assign(n_sys + 1, 0);
+    sys->nd_total = (int)didx.size();
+    for (int ty = 0; ty < 4; ty++) sys->term_off[ty].assign(n_sys + 1, 0);
     for (int b = 0; b < n_sys; b++) {
         sys->term_off[0][b + 1] = sys->term_off[0][b] + tops[b].n_bonds;
         sys->term_off[1][b + 1] = sys->term_off[1][b] + tops[b].n_angles;
         sys->term_off[2][b + 1] = sys->term_off[2][b] + tops[b].n_dihedrals;
+        sys->term_off[3][b + 1] = sys->term_off[3][b] + xcount[b];
     }
     std::vector<int2> sys_items;
     sys->sys_natoms.resize(n_sys);
@@ -415,6 +454,8 @@ ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t pre
     set_item_counts(sys, (int)items.size());
     c.n_bonds = (int)bidx.size();
     c.n_angles = (int)aidx.size();
+    c.n_dihedrals = (int)didx.size();
+    c.n_excl = (int)xidx.size();
     c.n_terms = n_terms;
     c.n_atoms = (int)total;
     c.vstride = ((3 * total + 31) / 32) * 32;
@@ -479,11 +520,17 @@ ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t pre
     CKC(upload(sys, &d_dpar, dpar));
     c.inc_off = d_inc_off; c.inc = d_inc; c.bidx = d_bidx; c.bpar = d_bpar;
     c.aidx = d_aidx; c.apar = d_apar; c.didx = d_didx; c.dpar = d_dpar;
+    int2 *d_xidx;
+    double *d_xw;
+    CKC(upload(sys, &d_xidx, xidx));
+    CKC(upload(sys, &d_xw, xw));
+    c.xidx = d_xidx;
+    c.xw = d_xw;
     int32_t *d_term_sys;
     CKC(upload(sys, &d_term_sys, term_sys));
     c.term_sys = d_term_sys;
     CKC(dalloc(sys, &c.te, std::max(n_terms, 1)));
-    CKC(dalloc(sys, &c.tg, 3 * (2 * bidx.size() + 3 * aidx.size() + 4 * didx.size()) + 3));
+    CKC(dalloc(sys, &c.tg, 3 * (2 * bidx.size() + 3 * aidx.size() + 4 * didx.size() + 2 * xidx.size()) + 3));
     CKC(dalloc(sys, &c.red, (size_t)c.n_tiles * NRED));
     CKC(dalloc(sys, &c.counters, CNT_N));
     CKC(dalloc(sys, &c.nactive, 1));

@@ -24,6 +24,32 @@ __device__ __forceinline__ void cross3(const double *a, const double *b, double 
     o[2] = a[0] * b[1] - a[1] * b[0];
 }
 
+// Exclusion correction (type 3, a force-field variant outside the paper):
+// w times the non-bonded pair term of atoms (i, j), w = s_ij - 1, in FP64:
+//   E = w (q'_i q'_j / r + r^-6 (C12 r^-6 - C6) / 6),
+//   grad_i E = w (e_cul + r^-6 (2 C12 r^-6 - C6)) r^-2 (x_j - x_i),
+// the same pair term the sweep adds, so that the sum is s_ij times it.
+__device__ inline double excl_term(const Ctx &c, const double *x, int term, double *gi, int ova,
+                                   const double *ov) {
+    const int2 ij = c.xidx[term];
+    const double w = c.xw[term];
+    double xi[3], xj[3], d[3];
+    ld3(x, ij.x, xi, ova, ov);
+    ld3(x, ij.y, xj, ova, ov);
+    for (int k = 0; k < 3; k++) d[k] = xj[k] - xi[k];
+    const double r2 = dot3(d, d);
+    const double ri = 1.0 / sqrt(r2), ri2 = ri * ri, ri6 = ri2 * ri2 * ri2;
+    const double2 pi = c.pard[ij.x], pj = c.pard[ij.y];
+    const double C6 = pi.x * pj.x, C12 = pi.y * pj.y;
+    const double ec = c.qs[ij.x] * c.qs[ij.y] * ri;
+    const double e = w * (ec + ri6 * (C12 * ri6 - C6) * (1.0 / 6.0));
+    if (gi) {
+        const double f = w * (ec + ri6 * (2.0 * C12 * ri6 - C6)) * ri2;
+        for (int k = 0; k < 3; k++) gi[k] = f * d[k];
+    }
+    return e;
+}
+
 // Energy of one bonded term; when g != nullptr also the gradient of the
 // term with respect to the atom at position `pos` of the term.
 //   bond     E = K (r - r0)^2
@@ -33,6 +59,12 @@ __device__ __forceinline__ void cross3(const double *a, const double *b, double 
 // sin phi = |b2| b1.n/(|m||n|) by the multiple-angle identities.
 __device__ inline double bonded_term(const Ctx &c, const double *x, int type, int term, int pos,
                               double *g, int *degenerate, int ova, const double *ov) {
+    if (type == 3) {
+        const double e = excl_term(c, x, term, g, ova, ov);
+        if (g && pos == 1)
+            for (int k = 0; k < 3; k++) g[k] = -g[k];
+        return e;
+    }
     if (type == 0) {
         const int2 ij = c.bidx[term];
         const double2 kp = c.bpar[term];
@@ -132,6 +164,11 @@ __device__ inline double bonded_term(const Ctx &c, const double *x, int type, in
 // term (g[p] for atom p of the term), the same formulas as bonded_term.
 __device__ inline double bonded_term_all(const Ctx &c, const double *x, int type, int term,
                                          double (*g)[3]) {
+    if (type == 3) {
+        const double e = excl_term(c, x, term, g ? g[0] : nullptr, -1, nullptr);
+        if (g) for (int k = 0; k < 3; k++) g[1][k] = -g[0][k];
+        return e;
+    }
     if (type == 0) {
         const double e = bonded_term(c, x, 0, term, 0, g ? g[0] : nullptr, nullptr, -1, nullptr);
         if (g) for (int k = 0; k < 3; k++) g[1][k] = -g[0][k];
@@ -217,14 +254,19 @@ __device__ inline double bonded_term_all(const Ctx &c, const double *x, int type
 }
 
 // global bonded-term index of (type, term) and the slot of its position
-// gradients: bonds first, then angles, then dihedrals
+// gradients: bonds first, then angles, dihedrals, exclusion corrections
 __device__ __forceinline__ int bonded_index(const Ctx &c, int type, int term) {
-    return type == 0 ? term : (type == 1 ? c.n_bonds + term : c.n_bonds + c.n_angles + term);
+    return type == 0 ? term
+                     : (type == 1 ? c.n_bonds + term
+                                  : (type == 2 ? c.n_bonds + c.n_angles + term
+                                               : c.n_bonds + c.n_angles + c.n_dihedrals + term));
 }
 __device__ __forceinline__ int64_t bonded_grad_slot(const Ctx &c, int type, int term, int pos) {
     return type == 0 ? 2LL * term + pos
                      : (type == 1 ? 2LL * c.n_bonds + 3LL * term + pos
-                                  : 2LL * c.n_bonds + 3LL * c.n_angles + 4LL * term + pos);
+                                  : (type == 2 ? 2LL * c.n_bonds + 3LL * c.n_angles + 4LL * term + pos
+                                               : 2LL * c.n_bonds + 3LL * c.n_angles + 4LL * c.n_dihedrals +
+                                                     2LL * term + pos));
 }
 
 // one bonded work item: every term of [t0, t0 + nt) whose system evaluates
@@ -237,12 +279,13 @@ __device__ inline void bonded_item(const Ctx &c, int t0, int nt, int mode) {
         int type, term;
         if (t < c.n_bonds) { type = 0; term = t; }
         else if (t < c.n_bonds + c.n_angles) { type = 1; term = t - c.n_bonds; }
-        else { type = 2; term = t - c.n_bonds - c.n_angles; }
+        else if (t < c.n_bonds + c.n_angles + c.n_dihedrals) { type = 2; term = t - c.n_bonds - c.n_angles; }
+        else { type = 3; term = t - c.n_bonds - c.n_angles - c.n_dihedrals; }
         double g[4][3];
         const bool grad = S.ev_kind == EV_EG;
         c.te[t] = bonded_term_all(c, x, type, term, grad ? g : nullptr);
         if (grad) {
-            const int np = type + 2;
+            const int np = type == 3 ? 2 : type + 2;
             double *dst = c.tg + 3 * bonded_grad_slot(c, type, term, 0);
             for (int p = 0; p < np; p++)
                 for (int k = 0; k < 3; k++) dst[3 * p + k] = g[p][k];

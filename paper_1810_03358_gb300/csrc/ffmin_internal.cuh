@@ -155,7 +155,10 @@ struct Ctx {
     const double2 *apar;
     const int4 *didx;
     const double4_32a *dpar;
-    int32_t n_bonds, n_angles, n_terms, n_pair_items;  // batch totals; bonded items follow pair items
+    int32_t n_bonds, n_angles, n_terms, n_pair_items;  // batch totals
+    int32_t n_dihedrals, n_excl;  // n_excl: exclusion corrections (type 3, after the dihedrals)
+    const int2 *xidx;             // [n_excl] atom pair of each correction
+    const double *xw;             // [n_excl] weight s_ij - 1 of its pair term
     const int32_t *term_sys;  // [n_terms] system of each bonded term
     const int2 *sys_items;  // [n_sys] (first, count) of each system's work items (contiguous)
     int32_t *act;           // per pair-kernel mode m: [m * (2 n_sys + 2)]: active systems, their

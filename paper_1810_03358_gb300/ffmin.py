@@ -36,7 +36,8 @@ class ffmin_topology(C.Structure):
                 ("n_bonds", C.c_int32), ("bond_idx", _ip), ("bond_k", _dp), ("bond_r0", _dp),
                 ("n_angles", C.c_int32), ("angle_idx", _ip), ("angle_k", _dp),
                 ("angle_theta0", _dp), ("n_dihedrals", C.c_int32), ("dihedral_idx", _ip),
-                ("dihedral_v", _dp), ("coulomb_c", C.c_double)]
+                ("dihedral_v", _dp), ("coulomb_c", C.c_double), ("exclusions", C.c_int32),
+                ("scale14", C.c_double)]
 
 
 class ffmin_options(C.Structure):
@@ -154,7 +155,8 @@ def _topology(s, keep):
                           int(arrs["bond_k"].size), i("bond_idx"), d("bond_k"), d("bond_r0"),
                           int(arrs["angle_k"].size), i("angle_idx"), d("angle_k"),
                           d("angle_theta0"), int(arrs["dihedral_v"].size // 4),
-                          i("dihedral_idx"), d("dihedral_v"), float(getattr(s, "coulomb_c", 0.0)))
+                          i("dihedral_idx"), d("dihedral_v"), float(getattr(s, "coulomb_c", 0.0)),
+                          int(getattr(s, "exclusions", 0)), float(getattr(s, "scale14", 0.5)))
 
 
 def _stream_handle(stream):

@@ -1,0 +1,116 @@
+"""GPU parity of the exclusion variant (bonded and angle-end pairs excluded,
+dihedral-end pairs scaled by scale14; a force-field option outside the
+paper) with the FP64 oracle, through the C ABI.  The GPU keeps its
+all-pairs sweep and adds FP64 correction terms of weight s_ij - 1, so the
+bars are those of the plain energy tests (FP64) plus the cancellation of
+the excluded terms: FP64 E within 2e-11 of sum|terms|, gradient within 1e-9
+of the largest force; MIXED at the jittered start E within 1e-5 of
+sum|terms| and gradient within 1e-4 of the largest force, plus 1e-6 of the
+all-pairs magnitudes (the FP32 rounding of the excluded terms)."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from paper_1810_03358_gb300 import synth
+from tests.gpu_util import need_gpu, split, to_dev
+from tests.test_gpu_minimize import ensemble_parity, prefix_parity, PREFIX, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: dict(e=2e-11, g=1e-9), 1: dict(e=1e-5, g=1e-4)}
+
+
+@pytest.fixture(scope="module")
+def ff():
+    return need_gpu()
+
+
+def excl(s, scale14=0.5):
+    return dataclasses.replace(s, exclusions=1, scale14=scale14)
+
+
+def check(ffmin, oracle_mod, systems, prec, xs=None):
+    xs = xs or [s.x for s in systems]
+    S = ffmin.System(systems, prec)
+    x = to_dev(xs)
+    e, g = S.energy_grad(x)
+    e_only = S.energy(x)
+    g = split(g.cpu().numpy(), systems)
+    S.close()
+    for b, s in enumerate(systems):
+        d, st, go = oracle_mod.energy_terms(s, xs[b], grad=True)
+        assert st == 0
+        e_tol = TOL[prec]["e"] * d["sum_abs"]
+        g_tol = TOL[prec]["g"] * np.abs(go).max()
+        if prec == 1 and getattr(s, "exclusions", 0):
+            # the FP32 sweep still carries the excluded terms (clashes of
+            # bonded neighbours, up to 1e8 kcal/mol at the jittered start)
+            # that the FP64 corrections cancel: their ~10 FP32 roundings
+            # (u = 6e-8) add 1e-6 of their magnitude
+            d0, _, g0 = oracle_mod.energy_terms(dataclasses.replace(s, exclusions=0), xs[b], grad=True)
+            e_tol += 1e-6 * d0["sum_abs"]
+            g_tol += 1e-6 * np.abs(g0).max()
+        assert abs(e[b] - d["total"]) <= e_tol, (b, e[b], d["total"])
+        assert abs(e_only[b] - e[b]) <= e_tol
+        assert np.abs(g[b] - go).max() <= g_tol, b
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("n", [3, 4, 64, 129, 300])
+def test_energy_gradient(ff, oracle_mod, prec, n):
+    check(ff, oracle_mod, [excl(synth.make_system(n, 600 + n))], prec)
+
+
+@pytest.mark.parametrize("scale14", [0.0, 1.0 / 1.2, 1.0])
+def test_scale14_values_and_mixed_batch(ff, oracle_mod, scale14):
+    # a batch mixing systems with and without exclusions
+    systems = [excl(synth.make_system(70, 610), scale14), synth.make_system(50, 611),
+               excl(synth.make_system(140, 612), scale14)]
+    check(ff, oracle_mod, systems, 0)
+
+
+def test_minimized_geometry_fp64(ff, oracle_mod):
+    s = excl(synth.make_system(120, 613))
+    xo, ro = oracle_mod.minimize(s, s.x, method=3)
+    assert ro["status_name"] == "ok"
+    check(ff, oracle_mod, [s], 0, [xo])
+
+
+def test_invalid_scale14_rejected(ff):
+    s = dataclasses.replace(synth.make_system(10, 614), exclusions=1, scale14=float("nan"))
+    with pytest.raises(ff.FfminError):
+        ff.System([s], 0)
+
+
+def test_lbfgs_prefix_and_full_run(ff, oracle_mod):
+    s = excl(synth.make_system(80, 615))
+    kw = dict(method=3, max_iter=PREFIX)
+    xg, rg, _ = run_gpu(ff, [s], 0, **kw)
+    prefix_parity(oracle_mod, s, xg[0], rg[0], kw)
+    kw = dict(method=3, max_iter=100000)
+    xg, rg, _ = run_gpu(ff, [s], 0, **kw)
+    ensemble_parity(oracle_mod, s, xg[0], rg[0], kw, members=3)
+
+
+def test_mixed_minimization_certified(ff, oracle_mod):
+    s = excl(synth.make_system(150, 616))
+    xg, rg, _ = run_gpu(ff, [s], 1, method=3, max_iter=100000)
+    r = rg[0]
+    assert r["status_name"] == "ok", r
+    e_true, g_true = oracle_mod.energy_grad(s, xg[0])
+    assert np.abs(g_true).max() < 0.1 * (1 + 1e-6)
+    assert abs(e_true - r["energy"]) <= 1e-9 * abs(e_true)
+
+
+def test_gradient_free_moves(ff, oracle_mod):
+    # the row energies of the moved atom include its exclusion corrections
+    s = excl(synth.make_system(90, 617))
+    kw = dict(method=4, max_iter=400, gtol_inf=1e-9, seed=77, gradfree_delta=0.05)
+    S = ff.System([s], 0)
+    x = to_dev([s.x])
+    r = S.minimize(x, **kw)[0]
+    S.close()
+    xo, ro = oracle_mod.minimize(s, s.x, **kw)
+    assert r["iterations"] == ro["iterations"] == 400
+    assert np.abs(x.cpu().numpy().reshape(-1, 3) - xo).max() < 1e-9
