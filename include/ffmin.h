@@ -90,7 +90,9 @@ typedef struct {
      * the paper: pairs joined by a bond or by the ends of an angle are
      * excluded, the end atoms of a dihedral interact scaled by scale14
      * (finite, >= 0).  Evaluated as FP64 correction terms (weight s - 1 on
-     * the pair term) beside the all-pairs sweep. */
+     * the pair term) beside the all-pairs sweep; FFMIN_FP64 only
+     * (ffmin_create rejects a MIXED batch with exclusions: the FP32 sweep's
+     * rounding of the excluded clashes would not cancel). */
     int32_t exclusions;
     double scale14;
 } ffmin_topology;

@@ -287,6 +287,12 @@ ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t pre
         if ((t.exclusions != 0 && t.exclusions != 1) ||
             (t.exclusions && !(t.scale14 >= 0.0 && std::isfinite(t.scale14))))
             return fail(nullptr, FFMIN_ERR_INVALID_ARG, "exclusions must be 0 or 1, scale14 finite and >= 0");
+        // the corrections cancel the excluded terms of the all-pairs sweep:
+        // exact in FP64, but the FP32 sweep's rounding of bonded-neighbour
+        // clashes (up to 1e10 kcal/mol at a jittered start) would swamp the
+        // energy, so exclusions run on the FP64 path only
+        if (t.exclusions && precision == FFMIN_MIXED)
+            return fail(nullptr, FFMIN_ERR_INVALID_ARG, "exclusions need precision FFMIN_FP64");
         total += t.n_atoms;
     }
     if (total > (1LL << 30)) return fail(nullptr, FFMIN_ERR_INVALID_ARG, "too many atoms");
