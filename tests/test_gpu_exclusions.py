@@ -50,6 +50,9 @@ def check(ffmin, oracle_mod, systems, prec, xs=None):
         e_tol = TOL[prec]["e"] * max(d["sum_abs"], d0["sum_abs"])
         g_tol = TOL[prec]["g"] * max(np.abs(go).max(), np.abs(g0).max())
         assert abs(e[b] - d["total"]) <= e_tol, (b, e[b], d["total"])
+        # and the stated bars against the variant's own terms
+        assert abs(e[b] - d["total"]) <= 1e-6 * d["sum_abs"]
+        assert np.abs(g[b] - go).max() <= 1e-4 * np.abs(go).max()
         assert abs(e_only[b] - e[b]) <= e_tol
         assert np.abs(g[b] - go).max() <= g_tol, b
 
