@@ -100,6 +100,11 @@ typedef struct {
     int32_t ls_par_K, ls_par_g0;
     double gradfree_delta;
     uint64_t seed;
+    /* gradient-free search: 0 = one atom at a time (Section 3); P >= 1 =
+     * parallel epochs over P slabs (Section 3's proposal), atoms closer
+     * than gradfree_margin A to a slab boundary stay put in that epoch */
+    int32_t gradfree_parts;
+    double gradfree_margin;
     const double *precond_d;   /* optional fixed per-variable H0 diagonal [n] (L-BFGS) */
     const double *mlp_w;       /* optional network [ORC_MLP_NW]: H0 diagonal per iteration (force field) */
     double ogm_step;           /* OGM: fixed step 1/L instead of the line search when > 0 (tests) */

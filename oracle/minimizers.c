@@ -581,6 +581,31 @@ static double ff_fg(void *ctx, const double *x, double *g, int32_t *status) {
     return t.total;
 }
 
+/* one gradient-free move of atom i in x: the best of 7 axis points (current,
+ * +-delta on x, y, z) and the vertex of the per-axis parabolas (8 row
+ * energies, Section 3) */
+static void parab_move(const orc_ff *ff, double *x, int32_t i, double dl) {
+    double p[8][3], fv[8];
+    for (int c = 0; c < 8; c++)
+        for (int a = 0; a < 3; a++) p[c][a] = x[3 * i + a];
+    for (int a = 0; a < 3; a++) {
+        p[1 + 2 * a][a] += dl; /* +delta */
+        p[2 + 2 * a][a] -= dl; /* -delta */
+    }
+    for (int c = 0; c < 7; c++) fv[c] = orc_row_energy(ff, x, i, p[c]);
+    for (int a = 0; a < 3; a++) {
+        double fp = fv[1 + 2 * a], fm = fv[2 + 2 * a];
+        double curv = fm - 2.0 * fv[0] + fp;
+        double ts = curv > 0.0 ? dl * (fm - fp) / (2.0 * curv) : 0.0;
+        p[7][a] = x[3 * i + a] + ts;
+    }
+    fv[7] = orc_row_energy(ff, x, i, p[7]);
+    int best = 0;
+    for (int c = 1; c < 8; c++)
+        if (fv[c] < fv[best]) best = c;
+    for (int a = 0; a < 3; a++) x[3 * i + a] = p[best][a];
+}
+
 /* gradient-free "parab" (Section 3): move one random atom per step to the
  * best of 7 axis points (current, +-delta on x, y, z) and the vertex of the
  * per-axis parabolas; check |grad|_inf once per sweep of N moves. */
@@ -599,26 +624,8 @@ static int parab(const orc_ff *ff, double *x, const orc_options *op, orc_result 
             for (int32_t sweep = 0; sweep < n; sweep++) {
                 if (moves >= op->max_iter) { status = ORC_MAX_ITER; break; }
                 int32_t i = orc_pick_atom(op->seed, (uint64_t)moves, n);
-                double p[8][3], fv[8];
-                for (int c = 0; c < 8; c++)
-                    for (int a = 0; a < 3; a++) p[c][a] = x[3 * i + a];
-                for (int a = 0; a < 3; a++) {
-                    p[1 + 2 * a][a] += dl; /* +delta */
-                    p[2 + 2 * a][a] -= dl; /* -delta */
-                }
-                for (int c = 0; c < 7; c++) fv[c] = orc_row_energy(ff, x, i, p[c]);
-                for (int a = 0; a < 3; a++) {
-                    double fp = fv[1 + 2 * a], fm = fv[2 + 2 * a];
-                    double curv = fm - 2.0 * fv[0] + fp;
-                    double ts = curv > 0.0 ? dl * (fm - fp) / (2.0 * curv) : 0.0;
-                    p[7][a] = x[3 * i + a] + ts;
-                }
-                fv[7] = orc_row_energy(ff, x, i, p[7]);
+                parab_move(ff, x, i, dl);
                 ne += 8;
-                int best = 0;
-                for (int c = 1; c < 8; c++)
-                    if (fv[c] < fv[best]) best = c;
-                for (int a = 0; a < 3; a++) x[3 * i + a] = p[best][a];
                 moves++;
             }
             if (status == ORC_MAX_ITER) break;
@@ -646,7 +653,156 @@ static int parab(const orc_ff *ff, double *x, const orc_options *op, orc_result 
     return status;
 }
 
+/* ---- parallel epochs of the gradient-free search (Section 3's proposal) ----
+ * Epoch e cuts the molecule into P parts by recursive bisection: a set of
+ * atoms meant for p parts is ordered by (coordinate on its axis of largest
+ * extent, index) and split at rank round(|A| floor(p/2) / p) (halves up) plus a random
+ * shift in [-span/2, span/2], span = max(1, |A| / (2p)) (node k of the
+ * bisection tree draws pick(seed, 2^62 + e 2^20 + k, span)), clamped to
+ * [1, |A| - 1]; the cut plane lies halfway between the two atoms on either
+ * side, and the halves recurse (left first) into floor(p/2) and the rest.
+ * Each part is a box bounded by its cut planes.  An atom is movable when it
+ * is at least `margin` from every cut plane of its box.  Every part q then
+ * runs |L_q| moves (L_q: its movable atoms in index order; move m picks
+ * L_q[pick(seed, q 2^40 + e N + m, |L_q|)]) on its own copy of the epoch's
+ * starting positions: it sees its own moves and the other parts as they
+ * were at the start of the epoch.  The parts' atoms are then merged and the
+ * gradient checked.  A cap on the total moves truncates part q to
+ * max_iter - (moves so far) - (moves of parts < q).  With P = 1 this is the
+ * sequential method (one epoch = one sweep). */
+#define EPOCH_CUT_STREAM (1ULL << 62)
+typedef struct { double c; int32_t a; } rank_t;
+static int cmp_rank(const void *u, const void *v) {
+    const rank_t *x = (const rank_t *)u, *y = (const rank_t *)v;
+    if (x->c != y->c) return x->c < y->c ? -1 : 1;
+    return x->a < y->a ? -1 : (x->a > y->a ? 1 : 0);
+}
+
+typedef struct {
+    const double *x;
+    uint64_t seed, e;
+    int32_t *part;   /* [N] part of each atom */
+    double *box;     /* [P][6]: lo xyz, hi xyz */
+    int32_t next;    /* next part id */
+    rank_t *rk;      /* scratch [N] */
+} cut_ctx_t;
+
+static void bisect(cut_ctx_t *cc, int32_t *A, int32_t na, int32_t p, const double lo[3],
+                   const double hi[3], uint64_t node) {
+    if (p == 1) {
+        const int32_t q = cc->next++;
+        for (int32_t k = 0; k < na; k++) cc->part[A[k]] = q;
+        for (int k = 0; k < 3; k++) { cc->box[6 * q + k] = lo[k]; cc->box[6 * q + 3 + k] = hi[k]; }
+        return;
+    }
+    int axis = 0;
+    double ext[3];
+    for (int k = 0; k < 3; k++) {
+        double mn = cc->x[3 * A[0] + k], mx = mn;
+        for (int32_t t = 1; t < na; t++) {
+            mn = fmin(mn, cc->x[3 * A[t] + k]);
+            mx = fmax(mx, cc->x[3 * A[t] + k]);
+        }
+        ext[k] = mx - mn;
+    }
+    if (ext[1] > ext[axis]) axis = 1;
+    if (ext[2] > ext[axis]) axis = 2;
+    for (int32_t t = 0; t < na; t++) { cc->rk[t].c = cc->x[3 * A[t] + axis]; cc->rk[t].a = A[t]; }
+    qsort(cc->rk, (size_t)na, sizeof(rank_t), cmp_rank);
+    for (int32_t t = 0; t < na; t++) A[t] = cc->rk[t].a;
+    const int32_t p1 = p / 2;
+    const int32_t span = na / (2 * p) > 1 ? na / (2 * p) : 1;
+    /* round(na p1 / p), halves up, in integers */
+    int32_t c = (int32_t)((2LL * na * p1 + p) / (2LL * p)) +
+                orc_pick_atom(cc->seed, EPOCH_CUT_STREAM + (cc->e << 20) + node, span) - span / 2;
+    if (c < 1) c = 1;
+    if (c > na - 1) c = na - 1;
+    const double plane = 0.5 * (cc->x[3 * A[c - 1] + axis] + cc->x[3 * A[c] + axis]);
+    double hl[3] = {hi[0], hi[1], hi[2]}, lr[3] = {lo[0], lo[1], lo[2]};
+    hl[axis] = plane;
+    lr[axis] = plane;
+    bisect(cc, A, c, p1, lo, hl, 2 * node + 1);
+    bisect(cc, A + c, na - c, p - p1, lr, hi, 2 * node + 2);
+}
+
+static int parab_epochs(const orc_ff *ff, double *x, const orc_options *op, orc_result *res) {
+    const int32_t n = ff->n_atoms, P = op->gradfree_parts < n ? op->gradfree_parts : n;
+    const double dl = op->gradfree_delta, w = op->gradfree_margin;
+    size_t nb = sizeof(double) * 3 * (size_t)n;
+    double *g = malloc(nb), *xs = malloc(nb), *xv = malloc(nb);
+    double *box = malloc(sizeof(double) * 6 * (size_t)P);
+    rank_t *rk = malloc(sizeof(rank_t) * (size_t)n);
+    int32_t *part = malloc(sizeof(int32_t) * (size_t)n), *list = malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *all = malloc(sizeof(int32_t) * (size_t)n), *mov = malloc(sizeof(int32_t) * (size_t)P);
+    orc_terms t;
+    int status = orc_energy_terms(ff, x, g, &t);
+    int32_t neg = 1, ne = 0, moves = 0;
+    double ginf = infnorm(3 * n, g);
+    trace_reset();
+    if (status == ORC_OK && !(ginf < op->gtol_inf)) {
+        for (uint64_t e = 0;; e++) {
+            if (moves >= op->max_iter) { status = ORC_MAX_ITER; break; }
+            for (int32_t a = 0; a < n; a++) all[a] = a;
+            const double inf3[3] = {-HUGE_VAL, -HUGE_VAL, -HUGE_VAL}, sup3[3] = {HUGE_VAL, HUGE_VAL, HUGE_VAL};
+            cut_ctx_t cc = {x, op->seed, e, part, box, 0, rk};
+            bisect(&cc, all, n, P, inf3, sup3, 0);
+            memcpy(xs, x, nb);
+            int32_t off = 0, truncated = 0;
+            for (int32_t q = 0; q < P; q++) {
+                const double *bx = box + 6 * q;
+                int32_t m_q = 0;
+                for (int32_t a = 0; a < n; a++) {
+                    if (part[a] != q) continue;
+                    int ok = 1;
+                    for (int k = 0; k < 3; k++)
+                        if (xs[3 * a + k] - bx[k] < w || bx[3 + k] - xs[3 * a + k] < w) ok = 0;
+                    if (ok) list[m_q++] = a;
+                }
+                int32_t allowed = op->max_iter - moves - off;
+                if (allowed > m_q) allowed = m_q;
+                if (allowed < 0) allowed = 0;
+                if (allowed < m_q) truncated = 1;
+                mov[q] = allowed;
+                memcpy(xv, xs, nb);
+                for (int32_t m = 0; m < allowed; m++) {
+                    const uint64_t k = ((uint64_t)q << 40) + e * (uint64_t)n + (uint64_t)m;
+                    parab_move(ff, xv, list[orc_pick_atom(op->seed, k, m_q)], dl);
+                    ne += 8;
+                }
+                for (int32_t a = 0; a < n; a++)
+                    if (part[a] == q)
+                        for (int k = 0; k < 3; k++) x[3 * a + k] = xv[3 * a + k];
+                off += m_q;
+            }
+            for (int32_t q = 0; q < P; q++) moves += mov[q];
+            if (truncated) { status = ORC_MAX_ITER; break; }
+            status = orc_energy_terms(ff, x, g, &t);
+            neg++;
+            ginf = infnorm(3 * n, g);
+            trace_add(t.total, (double)off, 0.0, 0.0);
+            if (status != ORC_OK) break;
+            if (ginf < op->gtol_inf) break;
+            if (off == 0) { status = ORC_MAX_ITER; break; } /* nothing movable */
+        }
+    }
+    if (status == ORC_MAX_ITER) { /* report the returned point */
+        orc_energy_terms(ff, x, g, &t);
+        neg++;
+        ginf = infnorm(3 * n, g);
+    }
+    res->energy = t.total;
+    res->grad_inf = ginf;
+    res->iterations = moves;
+    res->energy_evals = ne;
+    res->grad_evals = neg;
+    res->ls_failures = 0;
+    res->status = status;
+    free(g); free(xs); free(xv); free(box); free(rk); free(part); free(list); free(all); free(mov);
+    return status;
+}
+
 int orc_minimize_ff(const orc_ff *ff, double *x, const orc_options *o, orc_result *res) {
+    if (o->method == ORC_GRADFREE && o->gradfree_parts >= 1) return parab_epochs(ff, x, o, res);
     if (o->method == ORC_GRADFREE) return parab(ff, x, o, res);
     orc_options op = *o;
     if (op.cg_restart_every <= 0) op.cg_restart_every = 3 * ff->n_atoms;

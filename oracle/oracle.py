@@ -46,7 +46,8 @@ class _Opt(C.Structure):
                 ("max_evals", C.c_int32), ("cg_restart_every", C.c_int32), ("h0", C.c_double),
                 ("k_plus", C.c_double), ("k_minus", C.c_double), ("eps_h", C.c_double),
                 ("ls_par_K", C.c_int32), ("ls_par_g0", C.c_int32),
-                ("gradfree_delta", C.c_double), ("seed", C.c_uint64), ("precond_d", _dp),
+                ("gradfree_delta", C.c_double), ("seed", C.c_uint64), ("gradfree_parts", C.c_int32),
+                ("gradfree_margin", C.c_double), ("precond_d", _dp),
                 ("mlp_w", _dp), ("ogm_step", C.c_double)]
 
 
