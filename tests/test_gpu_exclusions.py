@@ -109,4 +109,9 @@ def test_gradient_free_moves(ff, oracle_mod):
     S.close()
     xo, ro = oracle_mod.minimize(s, s.x, **kw)
     assert r["iterations"] == ro["iterations"] == 400
-    assert np.abs(x.cpu().numpy().reshape(-1, 3) - xo).max() < 1e-9
+    # same decision at every move (another choice moves an atom by ~delta);
+    # the parabola vertices inherit the rounding of the row energies, which
+    # here includes the cancelled clashes of the excluded neighbours
+    # (~1e-16 of 1e10 kcal/mol), hence 1e-6 A rather than the 1e-9 A of
+    # the plain force field
+    assert np.abs(x.cpu().numpy().reshape(-1, 3) - xo).max() < 1e-6
