@@ -388,7 +388,8 @@ def methods_3334(ffmin, torch, dev, s3, cap=3000, gradfree_sweeps=10):
     """Every minimizer of the paper from the same jittered start of the
     3,334-atom globule (10^4 variables), in FP64 and MIXED: to |grad E|_inf
     < 0.1 or `cap` iterations (the gradient-free search: `gradfree_sweeps`
-    sweeps of N moves).  One timed run each (CUDA events)."""
+    sweeps of N moves, one atom at a time and in parallel epochs over 64
+    parts).  One timed run each (CUDA events)."""
     x0 = torch.tensor(s3.x.reshape(-1), dtype=torch.float64, device=dev)
     res = {}
     for prec, tag in ((ffmin.FFMIN_FP64, "fp64"), (ffmin.FFMIN_MIXED, "mixed")):
@@ -396,14 +397,16 @@ def methods_3334(ffmin, torch, dev, s3, cap=3000, gradfree_sweeps=10):
         S.autotune(x0)
         if prec == ffmin.FFMIN_FP64:
             res["start_energy"] = S.energy_grad(x0.clone())[0][0]
-        for name in ("GD", "FGM", "CG", "LBFGS", "OGM", "GRADFREE"):
-            cap_m = gradfree_sweeps * s3.n_atoms if name == "GRADFREE" else cap
-            S.minimize(x0.clone(), method=name, max_iter=2)  # warm-up (graphs, buffers)
+        runs = [(m, m, {}) for m in ("GD", "FGM", "CG", "LBFGS", "OGM", "GRADFREE")]
+        runs.append(("GRADFREE_EPOCHS64", "GRADFREE", dict(gradfree_parts=64, gradfree_margin=1.0)))
+        for name, method, extra in runs:
+            cap_m = gradfree_sweeps * s3.n_atoms if method == "GRADFREE" else cap
+            S.minimize(x0.clone(), method=method, max_iter=2, **extra)  # warm-up (graphs, buffers)
             x = x0.clone()
             torch.cuda.synchronize()
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             ev0.record()
-            r = S.minimize(x, method=name, max_iter=cap_m)[0]
+            r = S.minimize(x, method=method, max_iter=cap_m, **extra)[0]
             ev1.record()
             torch.cuda.synchronize()
             res[f"{name}_{tag}"] = {"status": r["status_name"], "iterations": r["iterations"],

@@ -113,6 +113,15 @@ typedef struct {
     int32_t ls_par_g0;       /* LS_PAR uses the slope at 0 (G0), default 1 */
     double gradfree_delta;   /* GRADFREE axis offset (A), default 0.05 */
     uint64_t seed;           /* GRADFREE atom picker seed (SplitMix64 stream) */
+    /* GRADFREE, 0 (default): one atom at a time (Section 3).  P >= 1: parallel
+     * epochs (Section 3's proposal): each epoch cuts the system into P parts
+     * by recursive bisection at randomly shifted median ranks, every part
+     * moves its atoms that lie at least gradfree_margin A (default 1.0) from
+     * its cut planes on its own copy of the epoch's starting positions, one
+     * CUDA block per part; the parts are merged and the gradient checked
+     * after every epoch.  P = 1 is the sequential method. */
+    int32_t gradfree_parts;
+    double gradfree_margin;
     int32_t use_learned_precond; /* L-BFGS: scale H0 by the learned per-atom diagonal */
     int32_t max_ticks;       /* safety bound on device evaluation rounds; 0 -> max_evals + 64 */
     /* L-BFGS trajectory recording (training data of the preconditioner):

@@ -6,6 +6,8 @@
 // finalize) on the library's own stream and reads back one counter of
 // still-active systems per replay.
 #include <algorithm>
+#include <array>
+#include <limits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -29,8 +31,10 @@ void parab_state_init(void *host_buf, int n, int atom0, int mode, int max_moves,
                       double delta);
 size_t parab_offset_move();
 size_t parab_offset_stop();
+cudaError_t launch_epoch(const Ctx &c, const EpochArgs &a, int parts, cudaStream_t s);
 }  // namespace ffm
 static ffmin_status parab_minimize(ffmin_system *sys, const ffmin_options *o, ffmin_result *res);
+static ffmin_status epoch_minimize(ffmin_system *sys, const ffmin_options *o, ffmin_result *res);
 
 struct ffmin_system {
     int n_sys = 0;
@@ -54,6 +58,11 @@ struct ffmin_system {
     void *parab_state = nullptr;
     cudaGraphExec_t parab_graph = nullptr;
     int parab_grid = 0;
+    // parallel-epoch gradient-free path: per-part copies and part lists
+    int ep_parts = 0;
+    double *ep_view = nullptr;
+    float4 *ep_viewf = nullptr;
+    int32_t *ep_ints = nullptr;  // list [N], members [N], loff, moff [P + 1], allowed [P]
     // learned preconditioner
     bool have_precond = false;
     // stats of the last minimize
@@ -207,6 +216,7 @@ void ffmin_options_default(ffmin_options *o) {
     o->ls_par_K = 2;
     o->ls_par_g0 = 1;
     o->gradfree_delta = 0.05;
+    o->gradfree_margin = 1.0;
     o->seed = 12345;
     o->use_learned_precond = 0;
     o->max_ticks = 0;
@@ -751,6 +761,8 @@ static ffmin_status check_options(ffmin_system *sys, const ffmin_options *o) {
         !(o->eps_h > 0.0 && o->eps_h < 1.0) || o->ls_par_K < 2 || !(o->gtol_inf >= 0.0) || o->max_iter < 0 ||
         o->max_evals < 1)
         return fail(sys, FFMIN_ERR_INVALID_ARG, "line-search / stopping parameter out of range");
+    if (o->method == FFMIN_GRADFREE && (o->gradfree_parts < 0 || !(o->gradfree_margin >= 0.0)))
+        return fail(sys, FFMIN_ERR_INVALID_ARG, "GRADFREE needs gradfree_parts >= 0 and gradfree_margin >= 0");
     if (o->method == FFMIN_GRADFREE && (sys->n_sys != 1 || !(o->gradfree_delta > 0.0)))
         return fail(sys, FFMIN_ERR_INVALID_ARG, "GRADFREE needs one system and delta > 0");
     if (o->use_learned_precond && !sys->have_precond)
@@ -765,7 +777,7 @@ static ffmin_status minimize_dev(ffmin_system *sys, double *x_dev, const ffmin_o
     const size_t bytes = sizeof(double) * 3 * sys->n_atoms;
     if (o->method == FFMIN_GRADFREE) {
         CK(cudaMemcpyAsync(vslot(c, V_X), x_dev, bytes, cudaMemcpyDeviceToDevice, sys->stream));
-        ffmin_status st = parab_minimize(sys, o, res);
+        ffmin_status st = o->gradfree_parts >= 1 ? epoch_minimize(sys, o, res) : parab_minimize(sys, o, res);
         if (st != FFMIN_OK) return st;
         CK(cudaMemcpyAsync(x_dev, vslot(c, V_X), bytes, cudaMemcpyDeviceToDevice, sys->stream));
         return FFMIN_OK;
@@ -1057,6 +1069,181 @@ static ffmin_status parab_minimize(ffmin_system *sys, const ffmin_options *o, ff
         ginf = sys->hst[0].res_ginf;
         if (sys->hst[0].status == FFMIN_ERR_NONFINITE) { status = FFMIN_ERR_NONFINITE; break; }
         if (truncated) { status = FFMIN_ERR_MAX_ITER; break; }
+    }
+    res[0].energy = f;
+    res[0].grad_inf = ginf;
+    res[0].iterations = moves;
+    res[0].energy_evals = 8 * moves;
+    res[0].grad_evals = neg;
+    res[0].ls_failures = 0;
+    res[0].stop_reason = status;
+    sys->last_ticks = ticks;
+    sys->last_launches = launches;
+    sys->last_pairs = (int64_t)moves * 8 * (n - 1) + (int64_t)neg * n * (int64_t)(n - 1) / 2;
+    return FFMIN_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Parallel epochs of the gradient-free search (options.gradfree_parts >= 1).
+// The host cuts the parts every epoch (recursive bisection of the current
+// positions: a set meant for p parts is ordered by (coordinate on its axis of
+// largest extent, index) and split at rank round(|A| floor(p/2) / p), halves
+// up, plus a shift pick(seed, 2^62 + e 2^20 + node, span) - span / 2,
+// span = max(1, |A| / (2p)), clamped to [1, |A| - 1]; the cut plane lies
+// halfway between the atoms on either side; left half first), lists every
+// part's atoms and its movable atoms (at least `margin` from each cut plane
+// of its box, index order) and the moves each part may make under the cap;
+// one block per part then runs the epoch (k_epoch) and the gradient is
+// checked on the merged positions.
+static uint64_t host_splitmix64(uint64_t seed, uint64_t k) {
+    uint64_t z = seed + (k + 1) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+static int32_t host_pick(uint64_t seed, uint64_t k, int32_t n) {
+    return (int32_t)(((unsigned __int128)host_splitmix64(seed, k) * (uint64_t)n) >> 64);
+}
+
+struct Cutter {
+    const double *x;
+    uint64_t seed, e;
+    std::vector<int32_t> part;
+    std::vector<std::array<double, 6>> box;
+    void run(std::vector<int32_t> &A, size_t a0, size_t na, int p, std::array<double, 6> b, uint64_t node) {
+        if (p == 1) {
+            const int32_t q = (int32_t)box.size();
+            for (size_t t = a0; t < a0 + na; t++) part[A[t]] = q;
+            box.push_back(b);
+            return;
+        }
+        int axis = 0;
+        double ext[3];
+        for (int k = 0; k < 3; k++) {
+            double mn = x[3 * A[a0] + k], mx = mn;
+            for (size_t t = a0 + 1; t < a0 + na; t++) {
+                mn = std::min(mn, x[3 * A[t] + k]);
+                mx = std::max(mx, x[3 * A[t] + k]);
+            }
+            ext[k] = mx - mn;
+        }
+        if (ext[1] > ext[axis]) axis = 1;
+        if (ext[2] > ext[axis]) axis = 2;
+        std::sort(A.begin() + a0, A.begin() + a0 + na, [&](int32_t u, int32_t v) {
+            const double cu = x[3 * u + axis], cv = x[3 * v + axis];
+            return cu < cv || (cu == cv && u < v);
+        });
+        const int p1 = p / 2;
+        const int32_t span = std::max<int32_t>(1, (int32_t)(na / (2 * (size_t)p)));
+        int64_t c = (2LL * (int64_t)na * p1 + p) / (2LL * p) +
+                    host_pick(seed, (1ULL << 62) + (e << 20) + node, span) - span / 2;
+        c = std::max<int64_t>(1, std::min<int64_t>(c, (int64_t)na - 1));
+        const double plane = 0.5 * (x[3 * A[a0 + c - 1] + axis] + x[3 * A[a0 + c] + axis]);
+        std::array<double, 6> bl = b, br = b;
+        bl[3 + axis] = plane;
+        br[axis] = plane;
+        run(A, a0, (size_t)c, p1, bl, 2 * node + 1);
+        run(A, a0 + (size_t)c, na - (size_t)c, p - p1, br, 2 * node + 2);
+    }
+};
+
+static ffmin_status epoch_minimize(ffmin_system *sys, const ffmin_options *o, ffmin_result *res) {
+    Ctx &c = sys->c;
+    const int n = sys->hst[0].natoms;
+    const int P = std::min(o->gradfree_parts, n);
+    const int mode = sys->prec == FFMIN_MIXED ? 0 : 1;
+    if (sys->ep_parts < P) {  // per-part copies (kept for later runs)
+        for (void *p : {(void *)sys->ep_view, (void *)sys->ep_viewf, (void *)sys->ep_ints}) {
+            if (!p) continue;
+            cudaFree(p);
+            sys->allocs.erase(std::remove(sys->allocs.begin(), sys->allocs.end(), p), sys->allocs.end());
+        }
+        sys->ep_view = nullptr;
+        sys->ep_viewf = nullptr;
+        sys->ep_ints = nullptr;
+        CK(cudaMalloc(&sys->ep_view, sizeof(double) * 3 * (size_t)n * P));
+        sys->allocs.push_back(sys->ep_view);
+        if (sys->prec == FFMIN_MIXED) {
+            CK(cudaMalloc(&sys->ep_viewf, sizeof(float4) * (size_t)n * P));
+            sys->allocs.push_back(sys->ep_viewf);
+        }
+        CK(cudaMalloc(&sys->ep_ints, sizeof(int32_t) * (2 * (size_t)n + 3 * (size_t)P + 2)));
+        sys->allocs.push_back(sys->ep_ints);
+        sys->ep_parts = P;
+    }
+    int32_t *d_list = sys->ep_ints, *d_members = d_list + n, *d_loff = d_members + n;
+    int32_t *d_moff = d_loff + P + 1, *d_allowed = d_moff + P + 1;
+    ffmin_status st = eval_slot(sys, V_X, EV_EG);
+    if (st != FFMIN_OK) return st;
+    int32_t neg = 1, moves = 0, status = FFMIN_OK;
+    double f = sys->hst[0].res_f, ginf = sys->hst[0].res_ginf;
+    int64_t launches = 3, ticks = 0;
+    if (sys->hst[0].status == FFMIN_ERR_NONFINITE) status = FFMIN_ERR_NONFINITE;
+    std::vector<double> xh(3 * (size_t)n);
+    std::vector<int32_t> A(n), ints(2 * (size_t)n + 3 * (size_t)P + 2);
+    const double w = o->gradfree_margin;
+    const double inf = std::numeric_limits<double>::infinity();
+    bool report = false;  // a cap or an empty epoch: one more evaluation reports the point
+    for (uint64_t e = 0; status == FFMIN_OK && !(ginf < o->gtol_inf); e++) {
+        if (moves >= o->max_iter) { status = FFMIN_ERR_MAX_ITER; report = true; break; }
+        CK(cudaMemcpyAsync(xh.data(), vslot(c, V_X), sizeof(double) * xh.size(), cudaMemcpyDeviceToHost,
+                           sys->stream));
+        CK(cudaStreamSynchronize(sys->stream));
+        Cutter cut{xh.data(), o->seed, e, std::vector<int32_t>(n, 0), {}};
+        for (int a = 0; a < n; a++) A[a] = a;
+        cut.run(A, 0, (size_t)n, P, {-inf, -inf, -inf, inf, inf, inf}, 0);
+        int32_t *list = ints.data(), *members = list + n, *loff = members + n, *moff = loff + P + 1;
+        int32_t *allowed = moff + P + 1;
+        int32_t nl = 0, nm = 0, off = 0, sum = 0;
+        bool truncated = false;
+        for (int q = 0; q < P; q++) {
+            loff[q] = nl;
+            moff[q] = nm;
+            const std::array<double, 6> &b = cut.box[q];
+            for (int a = 0; a < n; a++) {
+                if (cut.part[a] != q) continue;
+                members[nm++] = a;
+                bool ok = true;
+                for (int k = 0; k < 3; k++)
+                    if (xh[3 * a + k] - b[k] < w || b[3 + k] - xh[3 * a + k] < w) ok = false;
+                if (ok) list[nl++] = a;
+            }
+            const int32_t m_q = nl - loff[q];
+            int64_t al = (int64_t)o->max_iter - moves - off;
+            al = std::max<int64_t>(0, std::min<int64_t>(al, m_q));
+            if (al < m_q) truncated = true;
+            allowed[q] = (int32_t)al;
+            sum += (int32_t)al;
+            off += m_q;
+        }
+        loff[P] = nl;
+        moff[P] = nm;
+        CK(cudaMemcpyAsync(sys->ep_ints, ints.data(), sizeof(int32_t) * ints.size(), cudaMemcpyHostToDevice,
+                           sys->stream));
+        EpochArgs ea{sys->ep_view, sys->ep_viewf, d_list, d_loff, d_allowed, d_members, d_moff,
+                     n, mode, o->seed, e, o->gradfree_delta};
+        CK(launch_epoch(c, ea, P, sys->stream));
+        launches += 1;
+        ticks += 1;
+        moves += sum;
+        if (truncated) { status = FFMIN_ERR_MAX_ITER; report = true; break; }
+        st = eval_slot(sys, V_X, EV_EG);
+        if (st != FFMIN_OK) return st;
+        neg++;
+        launches += 3;
+        f = sys->hst[0].res_f;
+        ginf = sys->hst[0].res_ginf;
+        if (sys->hst[0].status == FFMIN_ERR_NONFINITE) { status = FFMIN_ERR_NONFINITE; break; }
+        if (ginf < o->gtol_inf) break;
+        if (off == 0) { status = FFMIN_ERR_MAX_ITER; report = true; break; }
+    }
+    if (report) {
+        st = eval_slot(sys, V_X, EV_EG);
+        if (st != FFMIN_OK) return st;
+        neg++;
+        launches += 3;
+        f = sys->hst[0].res_f;
+        ginf = sys->hst[0].res_ginf;
     }
     res[0].energy = f;
     res[0].grad_inf = ginf;

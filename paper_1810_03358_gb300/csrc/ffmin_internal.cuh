@@ -197,4 +197,19 @@ cudaError_t launch_dir(const Ctx &c, int which, cudaStream_t s);
 cudaError_t launch_sysreduce(const Ctx &c, int stage, cudaStream_t s);
 int pair_grid_size(int mode);
 
+// arguments of one epoch of the parallel gradient-free search (one block
+// per part, each on its own copy of the positions)
+struct EpochArgs {
+    double *view;           // [P][3N] FP64 positions of each part's copy
+    float4 *viewf;          // [P][N] FP32 (x, y, z, q') copies (MIXED)
+    const int32_t *list;    // movable atoms of every part, concatenated
+    const int32_t *loff;    // [P + 1] offsets into list
+    const int32_t *allowed; // [P] moves of each part in this epoch
+    const int32_t *members; // atoms of every part, concatenated
+    const int32_t *moff;    // [P + 1] offsets into members
+    int n, mode;
+    uint64_t seed, epoch;
+    double delta;
+};
+
 }  // namespace ffm

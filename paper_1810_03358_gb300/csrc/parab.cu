@@ -204,4 +204,160 @@ void parab_state_init(void *host_buf, int n, int atom0, int mode, int max_moves,
 size_t parab_offset_move() { return offsetof(ParabState, move); }
 size_t parab_offset_stop() { return offsetof(ParabState, stop_at); }
 
+// ---------------------------------------------------------------------------
+// Parallel epochs of the gradient-free search (Section 3's proposal: cut the
+// molecule into parts, move atoms away from the cuts in every part at once,
+// merge, cut again).  One block per part q works on its own copy of the
+// epoch's starting positions (FP64 [3N] and, for MIXED, FP32 (x, y, z, q')),
+// so it sees its own moves and the other parts as they were at the start of
+// the epoch; moves are those of the sequential method (7 rows, per-axis
+// parabola vertices, the best of 8) with row sums reduced by the block in a
+// fixed order.  Move m of part q picks its movable atom list entry
+// pick(seed, q 2^40 + e N + m, |L_q|).  The host cuts the parts.
+constexpr int EPOCH_THREADS = 256;
+
+// row sums of NP positions of atom i over the part's copy: this thread's j
+template <int NP>
+__device__ void epoch_rows(const Ctx &c, const EpochArgs &a, const double *V, const float4 *Vf, int i,
+                           const double (*p)[3], double *acc) {
+    for (int q = 0; q < NP; q++) acc[q] = 0.0;
+    if (a.mode == 1) {
+        const double qi = c.qs[i];
+        const double2 ci = c.pard[i];
+        for (int j = threadIdx.x; j < a.n; j += blockDim.x) {
+            if (j == i) continue;
+            const double xj = V[3 * j], yj = V[3 * j + 1], zj = V[3 * j + 2];
+            const double2 cj = c.pard[j];
+            const double c6 = ci.x * cj.x, c12 = ci.y * cj.y, qq = qi * c.qs[j];
+            for (int q = 0; q < NP; q++) {
+                const double dx = xj - p[q][0], dy = yj - p[q][1], dz = zj - p[q][2];
+                const double r2 = dx * dx + dy * dy + dz * dz;
+                const double ri = rsqrt(r2);
+                const double ri2 = ri * ri, ri6 = ri2 * ri2 * ri2;
+                acc[q] += qq * ri + ri6 * (c12 * ri6 - c6) * (1.0 / 6.0);
+            }
+        }
+    } else {
+        const float qi = Vf[i].w;
+        const float2 ci = c.parf[i];
+        float pf[NP][3];
+        for (int q = 0; q < NP; q++)
+            for (int k = 0; k < 3; k++) pf[q][k] = (float)p[q][k];
+        for (int j = threadIdx.x; j < a.n; j += blockDim.x) {
+            if (j == i) continue;
+            const float4 pj = Vf[j];
+            const float2 cj = c.parf[j];
+            const float c6 = ci.x * cj.x, c12 = ci.y * cj.y, qq = qi * pj.w;
+            for (int q = 0; q < NP; q++) {
+                const float dx = pj.x - pf[q][0], dy = pj.y - pf[q][1], dz = pj.z - pf[q][2];
+                const float r2 = dx * dx + dy * dy + dz * dz;
+                const float ri = rsqrtf(r2);
+                const float ri2 = ri * ri, ri6 = ri2 * ri2 * ri2;
+                acc[q] += (double)(qq * ri + ri6 * (c12 * ri6 - c6) * (1.0f / 6.0f));
+            }
+        }
+    }
+}
+
+// fixed-order block sum of NP values (warp shuffles, then warps in order)
+template <int NP>
+__device__ void block_sum_bcast(double (&v)[NP], double *out) {
+    __shared__ double sh[EPOCH_THREADS / 32][8];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int q = 0; q < NP; q++) {
+        double x = v[q];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) sh[w][q] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < NP) {
+        double t = 0.0;
+        for (int k = 0; k < EPOCH_THREADS / 32; k++) t += sh[k][threadIdx.x];
+        out[threadIdx.x] = t;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(EPOCH_THREADS) k_epoch(Ctx c, EpochArgs a) {
+    const int qp = blockIdx.x;
+    double *V = a.view + (int64_t)qp * 3 * a.n;
+    float4 *Vf = a.mode == 0 ? a.viewf + (int64_t)qp * a.n : nullptr;
+    const double *X = vslot(c, V_X);
+    for (int j = threadIdx.x; j < a.n; j += blockDim.x) {
+        for (int k = 0; k < 3; k++) V[3 * j + k] = X[3 * j + k];
+        if (Vf) Vf[j] = make_float4((float)X[3 * j], (float)X[3 * j + 1], (float)X[3 * j + 2], (float)c.qs[j]);
+    }
+    __syncthreads();
+    const int l0 = a.loff[qp], cnt = a.loff[qp + 1] - l0, moves = a.allowed[qp];
+    __shared__ double tot[8];
+    __shared__ double pv[3];
+    __shared__ int atom;
+    for (int m = 0; m < moves; m++) {
+        if (threadIdx.x == 0)
+            atom = a.list[l0 + pick_atom(a.seed, ((uint64_t)qp << 40) + a.epoch * (uint64_t)a.n + (uint64_t)m, cnt)];
+        __syncthreads();
+        const int i = atom;
+        double p[7][3];
+        for (int q = 0; q < 7; q++)
+            for (int k = 0; k < 3; k++) p[q][k] = V[3 * i + k];
+        for (int k = 0; k < 3; k++) {
+            p[1 + 2 * k][k] = p[1 + 2 * k][k] + a.delta;
+            p[2 + 2 * k][k] = p[2 + 2 * k][k] - a.delta;
+        }
+        double acc[7];
+        epoch_rows<7>(c, a, V, Vf, i, p, acc);
+        block_sum_bcast<7>(acc, tot);
+        if (threadIdx.x == 0) {
+            for (int q = 0; q < 7; q++) {  // bonded terms of atom i on this copy
+                double e = 0.0;
+                for (int k = c.inc_off[i]; k < c.inc_off[i + 1]; k++) {
+                    const int2 in = c.inc[k];
+                    e += bonded_term(c, V, in.x >> 2, in.y, in.x & 3, nullptr, nullptr, i, p[q]);
+                }
+                tot[q] += e;
+            }
+            for (int k = 0; k < 3; k++) {  // per-axis parabola vertex
+                const double fp = tot[1 + 2 * k], fm = tot[2 + 2 * k];
+                const double curv = fm - 2.0 * tot[0] + fp;
+                const double ts = curv > 0.0 ? a.delta * (fm - fp) / (2.0 * curv) : 0.0;
+                pv[k] = p[0][k] + ts;
+            }
+        }
+        __syncthreads();
+        double p7[1][3] = {{pv[0], pv[1], pv[2]}};
+        double acc7[1];
+        epoch_rows<1>(c, a, V, Vf, i, p7, acc7);
+        __shared__ double t7[1];
+        block_sum_bcast<1>(acc7, t7);
+        if (threadIdx.x == 0) {
+            double e = 0.0;
+            for (int k = c.inc_off[i]; k < c.inc_off[i + 1]; k++) {
+                const int2 in = c.inc[k];
+                e += bonded_term(c, V, in.x >> 2, in.y, in.x & 3, nullptr, nullptr, i, p7[0]);
+            }
+            const double f7 = t7[0] + e;
+            int best = 0;
+            double fb = tot[0];
+            for (int q = 1; q < 7; q++)
+                if (tot[q] < fb) { fb = tot[q]; best = q; }
+            const double *pb = best < 7 ? p[best] : p7[0];
+            if (f7 < fb) pb = p7[0];
+            for (int k = 0; k < 3; k++) V[3 * i + k] = pb[k];
+            if (Vf) Vf[i] = make_float4((float)pb[0], (float)pb[1], (float)pb[2], Vf[i].w);
+        }
+        __syncthreads();
+    }
+    // the part's atoms go back to X
+    double *Xw = vslot(c, V_X);
+    for (int t = a.moff[qp] + threadIdx.x; t < a.moff[qp + 1]; t += blockDim.x) {
+        const int j = a.members[t];
+        for (int k = 0; k < 3; k++) Xw[3 * j + k] = V[3 * j + k];
+    }
+}
+
+cudaError_t launch_epoch(const Ctx &c, const EpochArgs &a, int parts, cudaStream_t s) {
+    k_epoch<<<parts, EPOCH_THREADS, 0, s>>>(c, a);
+    return cudaGetLastError();
+}
+
 }  // namespace ffm

@@ -46,7 +46,8 @@ class ffmin_options(C.Structure):
                 ("max_evals", C.c_int32), ("cg_restart_every", C.c_int32), ("h0", C.c_double),
                 ("k_plus", C.c_double), ("k_minus", C.c_double), ("eps_h", C.c_double),
                 ("ls_par_K", C.c_int32), ("ls_par_g0", C.c_int32),
-                ("gradfree_delta", C.c_double), ("seed", C.c_uint64),
+                ("gradfree_delta", C.c_double), ("seed", C.c_uint64), ("gradfree_parts", C.c_int32),
+                ("gradfree_margin", C.c_double),
                 ("use_learned_precond", C.c_int32), ("max_ticks", C.c_int32),
                 ("record_dev", C.c_void_p), ("record_every", C.c_int32), ("record_slots", C.c_int32)]
 
