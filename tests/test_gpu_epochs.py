@@ -41,7 +41,10 @@ def test_epochs_match_oracle(ff, oracle_mod, n, P, margin, moves):
     for k in ("iterations", "energy_evals", "grad_evals"):
         assert rg[k] == ro[k], (k, rg, ro)
     assert rg["status_name"] == ro["status_name"] == "max_iter"
-    assert np.abs(xg - xo).max() < 1e-9
+    # same decision at every move (another choice moves an atom by ~delta);
+    # a vertex carries the rounding of its row-energy differences divided by
+    # the parabola's curvature (measured up to 2e-9 A)
+    assert np.abs(xg - xo).max() < 1e-8
     assert abs(rg["energy"] - ro["energy"]) <= 1e-10 * abs(ro["energy"])
 
 
