@@ -64,8 +64,11 @@ def test_epochs_with_exclusions(ff, oracle_mod):
     xg, rg, _ = run(ff, s, 0, **kw)
     xo, ro = oracle_mod.minimize(s, s.x, **kw)
     assert rg["iterations"] == ro["iterations"]
-    # vertices carry the rounding of the cancelled excluded clashes
-    assert np.abs(xg - xo).max() < 1e-6
+    # vertices carry the rounding of the cancelled excluded clashes (1e-16 of
+    # up to 1e10 kcal/mol in every row energy) over small curvatures; a
+    # different decision would move an atom by ~delta = 0.05 A
+    assert np.abs(xg - xo).max() < 1e-4
+    assert abs(rg["energy"] - ro["energy"]) <= 1e-9 * abs(ro["energy"])
 
 
 def test_mixed_epochs_lower_the_energy(ff, oracle_mod):
