@@ -13,7 +13,7 @@
  *           step 1/L replaced by a line search over h (the variant the
  *           paper gives right after Eq. 13)
  *
- * Readings where the paper is silent (also listed in the design notes):
+ * Readings where the paper is silent:
  *  - every search direction is normalised to unit 2-norm before the line
  *    search (Section 5.1), so h is the 2-norm of the step;
  *  - the step accepted in one search is the next search's h0 (Section 5.2);

@@ -10,7 +10,7 @@
 //
 // The machine restates, step for step, Algorithms 1-6 of arXiv 1810.03358
 // (Sections 5.1-5.2) and the adaptive gradient descent of Section 3 (Eq. 4),
-// with the readings documented in the design notes: normalised directions,
+// with these readings where the paper is silent: normalised directions,
 // warm-started steps, one restart after a failed line search, the
 // function-value momentum restart of FGM, skipped L-BFGS pairs with
 // <s, y> <= 0.  The L-BFGS two-loop recursion (Algorithm 3) is evaluated from

@@ -18,7 +18,7 @@ Two bars (FP64 path):
    rounding, separate (the landscape is rugged: measured agreement 1e-12 at
    300 steps, 1e-7 at 1000) and end in neighbouring minima.  The oracle's
    final energy is itself only defined up to that chaos, so a full run is
-   judged against an ensemble of oracle runs from starts perturbed by
+   compared with an ensemble of oracle runs from starts perturbed by
    1e-12 A: the GPU's final energy must lie within 0.01 % of the ensemble's
    range (or below it by at most the ensemble's own spread), or else within
    0.01 % of some further oracle run from a start perturbed by 1e-12 to
@@ -235,7 +235,7 @@ def test_full_runs_batched_ensemble(ff, oracle_mod):
 
 def test_paper_small_config_lbfgs_500(ff, oracle_mod):
     # 500-atom globule (seed 1), L-BFGS m = 10 to |grad|_inf < 0.1: exact for
-    # the capped prefix, then judged against a 3-member oracle ensemble
+    # the capped prefix, then compared with a 3-member oracle ensemble
     s = synth.make_system(500, 1)
     kw = dict(method=3, lbfgs_m=10, gtol_inf=0.1, max_iter=PREFIX)
     xg, rg, _ = run_gpu(ff, [s], 0, **kw)
