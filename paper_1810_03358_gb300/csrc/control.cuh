@@ -278,7 +278,7 @@ __device__ void lbfgs_pass1(SysState &S, int use_d);
 __device__ void ls_begin(const Ctx &c, SysState &S, double rr, double gr) {
     if (S.method == FFMIN_LBFGS && S.dir_used_d && !(gr < 0.0)) {
         // the learned diagonal gave no descent direction: plain L-BFGS for
-        // this iteration (next round: both direction passes again)
+        // this iteration (the next iteration runs both direction passes again)
         lbfgs_pass1(S, 0);
         return;
     }
