@@ -233,6 +233,14 @@ ffmin_status ffmin_autotune(ffmin_system *sys, const double *x_dev, int32_t *den
 ffmin_status ffmin_time_pair_kernel(ffmin_system *sys, const double *x_dev, int32_t with_grad,
                                     int32_t reps, float *ms);
 
+/* The parts of one epoch of the parallel gradient-free search, computed on
+ * the host exactly as ffmin_minimize cuts them (see gradfree_parts):
+ * part_out[a] = part of atom a (parts numbered left first in the bisection),
+ * movable_out[a] = 1 when atom a is at least margin A from every cut plane
+ * of its part.  x_host: [3n] positions; no device work.  Not in the paper. */
+ffmin_status ffmin_epoch_parts(const double *x_host, int32_t n, int32_t parts, uint64_t seed,
+                               uint64_t epoch, double margin, int32_t *part_out, int32_t *movable_out);
+
 /* Measured ALU peak of the current device in TFLOP/s (FMA = 2 flops):
  * independent FP32 (precision = FFMIN_MIXED) or FP64 (FFMIN_FP64) FMA
  * chains on every SM, reps timed launches on the default stream after three

@@ -1257,3 +1257,25 @@ static ffmin_status epoch_minimize(ffmin_system *sys, const ffmin_options *o, ff
     sys->last_pairs = (int64_t)moves * 8 * (n - 1) + (int64_t)neg * n * (int64_t)(n - 1) / 2;
     return FFMIN_OK;
 }
+
+extern "C" ffmin_status ffmin_epoch_parts(const double *x_host, int32_t n, int32_t parts, uint64_t seed,
+                                          uint64_t epoch, double margin, int32_t *part_out,
+                                          int32_t *movable_out) {
+    if (!x_host || n < 1 || parts < 1 || !part_out || !movable_out || !(margin >= 0.0))
+        return FFMIN_ERR_INVALID_ARG;
+    const int P = std::min<int32_t>(parts, n);
+    const double inf = std::numeric_limits<double>::infinity();
+    Cutter cut{x_host, seed, epoch, std::vector<int32_t>(n, 0), {}};
+    std::vector<int32_t> A(n);
+    for (int a = 0; a < n; a++) A[a] = a;
+    cut.run(A, 0, (size_t)n, P, {-inf, -inf, -inf, inf, inf, inf}, 0);
+    for (int a = 0; a < n; a++) {
+        part_out[a] = cut.part[a];
+        const std::array<double, 6> &b = cut.box[cut.part[a]];
+        bool ok = true;
+        for (int k = 0; k < 3; k++)
+            if (x_host[3 * a + k] - b[k] < margin || b[3 + k] - x_host[3 * a + k] < margin) ok = false;
+        movable_out[a] = ok ? 1 : 0;
+    }
+    return FFMIN_OK;
+}

@@ -63,7 +63,8 @@ EXPORTS = ["ffmin_options_default", "ffmin_status_string", "ffmin_create", "ffmi
            "ffmin_energy_grad_host", "ffmin_minimize", "ffmin_minimize_host",
            "ffmin_set_precond", "ffmin_time_pair_kernel", "ffmin_last_stats",
            "ffmin_last_error", "ffmin_pair_energy_grad_noalloc", "ffmin_neighbour_counts",
-           "ffmin_mlp_train", "ffmin_mlp_work_floats", "ffmin_autotune", "ffmin_alu_peak"]
+           "ffmin_mlp_train", "ffmin_mlp_work_floats", "ffmin_autotune", "ffmin_alu_peak",
+           "ffmin_epoch_parts"]
 
 _lib = None
 
@@ -89,6 +90,7 @@ def lib():
     L.ffmin_atom_offset.argtypes = [vp, C.c_int32]
     L.ffmin_atom_offset.restype = C.c_int64
     L.ffmin_alu_peak.argtypes = [C.c_int32, C.c_int32, _dp]
+    L.ffmin_epoch_parts.argtypes = [_dp, C.c_int32, C.c_int32, C.c_uint64, C.c_uint64, C.c_double, _ip, _ip]
     L.ffmin_energy.argtypes = [vp, vp, _dp]
     L.ffmin_energy_grad.argtypes = [vp, vp, _dp, vp]
     L.ffmin_energy_grad_host.argtypes = [vp, _dp, _dp, _dp]
@@ -273,6 +275,18 @@ def ffmin_time_pair_kernel(handle, x, with_grad=True, reps=10):
                                       int(with_grad), int(reps), C.byref(ms))
     _check(st, handle)
     return ms.value
+
+
+def ffmin_epoch_parts(x, parts, seed, epoch, margin):
+    """Host-side parts of one epoch of the parallel gradient-free search:
+    (part of each atom, movable flags) for positions x [N, 3] (numpy)."""
+    xx = np.ascontiguousarray(x, dtype=np.float64).reshape(-1)
+    n = xx.size // 3
+    part = np.zeros(n, dtype=np.int32)
+    mov = np.zeros(n, dtype=np.int32)
+    _check(lib().ffmin_epoch_parts(xx.ctypes.data_as(_dp), n, int(parts), int(seed), int(epoch),
+                                   float(margin), part.ctypes.data_as(_ip), mov.ctypes.data_as(_ip)))
+    return part, mov.astype(bool)
 
 
 def ffmin_alu_peak(precision, reps=10):

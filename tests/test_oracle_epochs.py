@@ -112,3 +112,19 @@ def test_epochs_lower_the_energy(oracle_mod):
     e1 = oracle_mod.energy(s, xo)
     assert e1 < 1e-2 * e0
     assert ro["energy"] == pytest.approx(e1, rel=1e-12)
+
+
+@pytest.mark.parametrize("n,P,seed", [(14, 2, 11), (300, 8, 99), (1000, 64, 5), (3334, 128, 3)])
+def test_library_host_cut_matches_the_rules(oracle_mod, n, P, seed):
+    # the CUDA library cuts the parts on the host: its cut (no GPU needed)
+    # equals the rules restated above, which the oracle's moves also match
+    from paper_1810_03358_gb300 import build, ffmin
+    build.build()
+    s = synth.make_system(n, 740 + n)
+    for e in (0, 3):
+        part, mov = ffmin.ffmin_epoch_parts(s.x, P, seed, e, 0.5)
+        ref, boxes = partition(oracle_mod, s.x, e, P, seed)
+        assert np.array_equal(part, ref)
+        ref_mov = [bool(np.all(s.x[a] - boxes[ref[a]][0] >= 0.5) and np.all(boxes[ref[a]][1] - s.x[a] >= 0.5))
+                   for a in range(n)]
+        assert np.array_equal(mov, ref_mov)
