@@ -71,9 +71,13 @@ __device__ void row_partial(const Ctx &c, int mode, int atom0, int n, int i, con
     } else {
         const float qi = c.posf[atom0 + i].w;
         const float2 ci = c.parf[atom0 + i];
-        float pf[NP][3];
-        for (int q = 0; q < NP; q++)
+        float pf[NP][3], accf[NP];
+        for (int q = 0; q < NP; q++) {
+            accf[q] = 0.f;
             for (int a = 0; a < 3; a++) pf[q][a] = (float)p[q][a];
+        }
+        // FP32 sums of this thread's j (tile-local FP32 accumulation of the
+        // mixed form), FP64 from the block reduction on
         for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
             if (j == i) continue;
             const float4 pj = c.posf[atom0 + j];
@@ -84,9 +88,10 @@ __device__ void row_partial(const Ctx &c, int mode, int atom0, int n, int i, con
                 const float r2 = dx * dx + dy * dy + dz * dz;
                 const float ri = rsqrtf(r2);
                 const float ri2 = ri * ri, ri6 = ri2 * ri2 * ri2;
-                acc[q] += (double)(qq * ri + ri6 * (c12 * ri6 - c6) * (1.0f / 6.0f));
+                accf[q] += qq * ri + ri6 * (c12 * ri6 - c6) * (1.0f / 6.0f);
             }
         }
+        for (int q = 0; q < NP; q++) acc[q] = (double)accf[q];
     }
 }
 
@@ -240,10 +245,12 @@ __device__ void epoch_rows(const Ctx &c, const EpochArgs &a, const double *V, co
     } else {
         const float qi = Vf[i].w;
         const float2 ci = c.parf[i];
-        float pf[NP][3];
-        for (int q = 0; q < NP; q++)
+        float pf[NP][3], accf[NP];
+        for (int q = 0; q < NP; q++) {
+            accf[q] = 0.f;
             for (int k = 0; k < 3; k++) pf[q][k] = (float)p[q][k];
-        for (int j = threadIdx.x; j < a.n; j += blockDim.x) {
+        }
+        for (int j = threadIdx.x; j < a.n; j += blockDim.x) {  // FP32 sums of this thread's j
             if (j == i) continue;
             const float4 pj = Vf[j];
             const float2 cj = c.parf[j];
@@ -253,9 +260,10 @@ __device__ void epoch_rows(const Ctx &c, const EpochArgs &a, const double *V, co
                 const float r2 = dx * dx + dy * dy + dz * dz;
                 const float ri = rsqrtf(r2);
                 const float ri2 = ri * ri, ri6 = ri2 * ri2 * ri2;
-                acc[q] += (double)(qq * ri + ri6 * (c12 * ri6 - c6) * (1.0f / 6.0f));
+                accf[q] += qq * ri + ri6 * (c12 * ri6 - c6) * (1.0f / 6.0f);
             }
         }
+        for (int q = 0; q < NP; q++) acc[q] = (double)accf[q];
     }
 }
 
@@ -307,15 +315,17 @@ __global__ void __launch_bounds__(EPOCH_THREADS) k_epoch(Ctx c, EpochArgs a) {
         double acc[7];
         epoch_rows<7>(c, a, V, Vf, i, p, acc);
         block_sum_bcast<7>(acc, tot);
-        if (threadIdx.x == 0) {
-            for (int q = 0; q < 7; q++) {  // bonded terms of atom i on this copy
-                double e = 0.0;
-                for (int k = c.inc_off[i]; k < c.inc_off[i + 1]; k++) {
-                    const int2 in = c.inc[k];
-                    e += bonded_term(c, V, in.x >> 2, in.y, in.x & 3, nullptr, nullptr, i, p[q]);
-                }
-                tot[q] += e;
+        if (threadIdx.x < 7) {  // bonded terms of atom i on this copy, one position per thread
+            const int q = threadIdx.x;
+            double e = 0.0;
+            for (int k = c.inc_off[i]; k < c.inc_off[i + 1]; k++) {
+                const int2 in = c.inc[k];
+                e += bonded_term(c, V, in.x >> 2, in.y, in.x & 3, nullptr, nullptr, i, p[q]);
             }
+            tot[q] += e;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
             for (int k = 0; k < 3; k++) {  // per-axis parabola vertex
                 const double fp = tot[1 + 2 * k], fm = tot[2 + 2 * k];
                 const double curv = fm - 2.0 * tot[0] + fp;
