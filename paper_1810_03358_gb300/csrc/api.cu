@@ -1129,16 +1129,22 @@ struct Cutter {
         }
         if (ext[1] > ext[axis]) axis = 1;
         if (ext[2] > ext[axis]) axis = 2;
-        std::sort(A.begin() + a0, A.begin() + a0 + na, [&](int32_t u, int32_t v) {
-            const double cu = x[3 * u + axis], cv = x[3 * v + axis];
-            return cu < cv || (cu == cv && u < v);
-        });
         const int p1 = p / 2;
         const int32_t span = std::max<int32_t>(1, (int32_t)(na / (2 * (size_t)p)));
         int64_t c = (2LL * (int64_t)na * p1 + p) / (2LL * p) +
                     host_pick(seed, (1ULL << 62) + (e << 20) + node, span) - span / 2;
         c = std::max<int64_t>(1, std::min<int64_t>(c, (int64_t)na - 1));
-        const double plane = 0.5 * (x[3 * A[a0 + c - 1] + axis] + x[3 * A[a0 + c] + axis]);
+        // the order (coordinate, index) is strict, so the c smallest atoms
+        // and the atoms on either side of the cut are unique: a selection
+        // (linear time) instead of a sort
+        auto less = [&](int32_t u, int32_t v) {
+            const double cu = x[3 * u + axis], cv = x[3 * v + axis];
+            return cu < cv || (cu == cv && u < v);
+        };
+        std::nth_element(A.begin() + a0, A.begin() + a0 + c, A.begin() + a0 + na, less);
+        const int32_t right = A[a0 + c];
+        const int32_t left = *std::max_element(A.begin() + a0, A.begin() + a0 + c, less);
+        const double plane = 0.5 * (x[3 * left + axis] + x[3 * right + axis]);
         std::array<double, 6> bl = b, br = b;
         bl[3 + axis] = plane;
         br[axis] = plane;
@@ -1194,15 +1200,21 @@ static ffmin_status epoch_minimize(ffmin_system *sys, const ffmin_options *o, ff
         cut.run(A, 0, (size_t)n, P, {-inf, -inf, -inf, inf, inf, inf}, 0);
         int32_t *list = ints.data(), *members = list + n, *loff = members + n, *moff = loff + P + 1;
         int32_t *allowed = moff + P + 1;
-        int32_t nl = 0, nm = 0, off = 0, sum = 0;
+        int32_t nl = 0, off = 0, sum = 0;
         bool truncated = false;
+        // members of every part in index order (counting sort by part)
+        for (int q = 0; q <= P; q++) moff[q] = 0;
+        for (int a = 0; a < n; a++) moff[cut.part[a] + 1]++;
+        for (int q = 0; q < P; q++) moff[q + 1] += moff[q];
+        {
+            std::vector<int32_t> fill(moff, moff + P);
+            for (int a = 0; a < n; a++) members[fill[cut.part[a]]++] = a;
+        }
         for (int q = 0; q < P; q++) {
             loff[q] = nl;
-            moff[q] = nm;
             const std::array<double, 6> &b = cut.box[q];
-            for (int a = 0; a < n; a++) {
-                if (cut.part[a] != q) continue;
-                members[nm++] = a;
+            for (int t = moff[q]; t < moff[q + 1]; t++) {
+                const int a = members[t];
                 bool ok = true;
                 for (int k = 0; k < 3; k++)
                     if (xh[3 * a + k] - b[k] < w || b[3 + k] - xh[3 * a + k] < w) ok = false;
@@ -1217,7 +1229,6 @@ static ffmin_status epoch_minimize(ffmin_system *sys, const ffmin_options *o, ff
             off += m_q;
         }
         loff[P] = nl;
-        moff[P] = nm;
         CK(cudaMemcpyAsync(sys->ep_ints, ints.data(), sizeof(int32_t) * ints.size(), cudaMemcpyHostToDevice,
                            sys->stream));
         EpochArgs ea{sys->ep_view, sys->ep_viewf, d_list, d_loff, d_allowed, d_members, d_moff,
