@@ -239,12 +239,20 @@ def bench_gpu(args):
     # dominant kernel: FP64 pair kernel, E + grad mode, timed alone on its stream
     ms_pair = S64.time_pair_kernel(x0, with_grad=True, reps=5)
     ms_pair_e = S64.time_pair_kernel(x0, with_grad=False, reps=5)
+    e64, g64 = S64.energy_grad(x0.clone())
+    g64 = g64.cpu().numpy()
     S64.close()
     # ---- mixed precision, same step ----
     S32 = ffmin.System([s], ffmin.FFMIN_MIXED)
     density32 = S32.autotune(x0)
     t32, ev32, launches32, r32 = run_steps(S32, args.steps, args.warmup)
     ms_pair32 = S32.time_pair_kernel(x0, with_grad=True, reps=20)
+    # error of one MIXED E + grad at the start against the FP64 path (which
+    # the parity tests hold to 2e-11 of sum|terms| of the FP64 oracle)
+    e32, g32 = S32.energy_grad(x0.clone())
+    g32 = g32.cpu().numpy()
+    mixed_err = {"energy_rel": abs(e32[0] - e64[0]) / abs(e64[0]),
+                 "grad_rel_to_max": float(np.abs(g32 - g64).max() / np.abs(g64).max())}
     S32.close()
     t32_tot, pairs32 = reduce_time_units(sum(t32), sum(ev32) * pairs_per_eval, dev)
     value32 = pairs32 / t32_tot
@@ -296,6 +304,7 @@ def bench_gpu(args):
                   "autotuned_items_per_block": density32,
                   "vs_plain_gpu": value32 / value,
                   "final_energy": r32["energy"], "final_energy_fp64": r64["energy"],
+                  "error_vs_fp64_at_start": mixed_err,
                   "roofline": {"bound": "alu", "kernel": "k_pair<float,64,2> E+grad",
                                "achieved": achieved_fp32, "peak": fp32_peak, "unit": "TFLOP/s",
                                "frac": achieved_fp32 / fp32_peak, "ms_per_launch": ms_pair32,
