@@ -498,6 +498,18 @@ def profile_run(args):
         print("profile-batch", st, "ms", ev0.elapsed_time(ev1), "ms/tick", ev0.elapsed_time(ev1) / st["ticks"])
         S.close()
         return
+    if args.profile_epochs:
+        # one epoch of the parallel gradient-free search on the 30,000-atom
+        # globule, MIXED, 128 parts (the k_epoch workload)
+        s = synth.make_system(N_ATOMS, SEED)
+        S = ffmin.System([s], ffmin.FFMIN_MIXED)
+        x = torch.tensor(s.x.reshape(-1), dtype=torch.float64, device="cuda")
+        r = S.minimize(x, method="GRADFREE", max_iter=args.profile_epochs, gradfree_parts=128,
+                       gradfree_margin=1.0)
+        torch.cuda.synchronize()
+        print("profile-epochs", r[0]["iterations"], S.last_stats())
+        S.close()
+        return
     if args.profile_vectors:
         # 1,024 systems of 500 atoms (512,000 atoms, vectors of 12.3 MB; 64
         # chains, each under 16 coordinate jitters): FP64
@@ -561,6 +573,7 @@ def main():
     ap.add_argument("--profile-minimize", type=int, default=0)
     ap.add_argument("--profile-batch", type=int, default=0)
     ap.add_argument("--profile-vectors", type=int, default=0)
+    ap.add_argument("--profile-epochs", type=int, default=0)
     args = ap.parse_args()
     if args.profile:
         profile_run(args)
