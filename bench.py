@@ -382,7 +382,7 @@ def minimizations(args, ffmin, synth, torch, dev, rank=0, ws=1):
         out["sample4_mixed_learned"] = run(sample, ffmin.FFMIN_MIXED, learned=True)
         out["sample4_mixed_learned_vs_plain_gpu"] = ratio("sample4_mixed_learned", "sample4_fp64")
     s3 = synth.make_system(3334, 2)
-    if not getattr(args, "no_methods", False):
+    if not getattr(args, "no_methods", False) and ws == 1:  # per-method runs: single-GPU runs only
         out["methods_3334"] = methods_3334(ffmin, torch, dev, s3)
     out["n3334_fp64"] = run([s3], ffmin.FFMIN_FP64)
     out["n3334_mixed"] = run([s3], ffmin.FFMIN_MIXED)
