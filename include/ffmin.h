@@ -5,10 +5,14 @@
  * The operations follow arXiv 1810.03358 ("Algorithms for local minimization
  * of a force field for 3D macromolecules"):
  *   - energy: Section 2, E = E_stretch + E_bend + E_torsion + E_cul + E_vdw,
- *     non-bonded terms over ALL atom pairs (no exclusions), explicit gradient;
+ *     non-bonded terms over ALL atom pairs (no exclusions, unless a topology
+ *     asks for the exclusion variant, which the paper does not have),
+ *     explicit gradient;
  *   - minimizers: Section 5.1, Algorithms 1 (FGM), 2 (CG), 3-4 (L-BFGS);
  *     adaptive gradient descent of Section 3 (Eq. 4 with a parabolic step);
- *     the gradient-free random-atom "parab" moves of Section 3;
+ *     the gradient-free random-atom "parab" moves of Section 3, one atom at
+ *     a time or in parallel epochs (Section 3's proposal); the optimized
+ *     gradient method of Section 4 (Eq. 11) with a line search;
  *   - line searches: Section 5.2, Algorithms 5 (LS_H) and 6 (LS_PAR).
  *
  * Conventions
