@@ -156,11 +156,16 @@ def flush_l2(buf):
     buf.zero_()
 
 
-def step_config():
-    """The workload of one benchmark step (both arms)."""
-    return {"workload": f"{N_ATOMS}-atom chain globule (seed {SEED}), plain FP64 path, "
-                        f"L-BFGS m=10 capped at {CAP_ITERS} steps per step",
-            "n_atoms": N_ATOMS, "l2": "flushed (256 MB write) between steps"}
+def step_config(system=None):
+    """The workload of one benchmark step (both arms), with the SHA-256 of
+    the generated inputs when the system is given."""
+    out = {"workload": f"{N_ATOMS}-atom chain globule (seed {SEED}), plain FP64 path, "
+                       f"L-BFGS m=10 capped at {CAP_ITERS} steps per step",
+           "n_atoms": N_ATOMS, "l2": "flushed (256 MB write) between steps"}
+    if system is not None:
+        from paper_1810_03358_gb300 import synth
+        out["input_sha256"] = synth.digest(system)
+    return out
 
 
 def bench_gpu(args):
@@ -284,7 +289,7 @@ def bench_gpu(args):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": dict(step_config(), evals_per_step=ev64[0], autotuned_items_per_block=density64,
+        "config": dict(step_config(s), evals_per_step=ev64[0], autotuned_items_per_block=density64,
                        parallelism=f"replicas x{ws}"),
         "e2e": {"value": e2e_value, "unit": "pair interactions/s",
                 "h2d_bytes_per_step": 8 * 3 * N_ATOMS, "d2h_bytes_per_step": 8 * 3 * N_ATOMS},
@@ -462,7 +467,7 @@ def bench_reference(args):
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": step_config(),
+        "config": step_config(s),
         "cpu_baseline": {"value": value, "unit": "pair interactions/s", "cores": 1, "kind": "oracle",
                          "sample": "one full E+grad evaluation of the 30,000-atom globule per step "
                                    "(a bounded sample of the step's 41 evaluations)"},

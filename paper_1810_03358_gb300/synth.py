@@ -17,6 +17,7 @@ one of Section 2 (stretch, bend, torsion, Coulomb, Lennard-Jones).
 """
 from __future__ import annotations
 
+import hashlib
 import math
 from dataclasses import dataclass, field
 
@@ -250,3 +251,36 @@ def rigid_motion(rng: np.random.Generator):
         qm[:, 0] = -qm[:, 0]
     t = rng.normal(scale=5.0, size=3)
     return qm, t
+
+
+_ARRAYS = ("x", "charge", "sigma", "epsilon", "bond_idx", "bond_k", "bond_r0", "angle_idx", "angle_k",
+           "angle_theta0", "dihedral_idx", "dihedral_v")
+
+
+def digest(s: System) -> str:
+    """SHA-256 over the system's coordinates, parameters and topology (the
+    exact inputs a run consumed)."""
+    h = hashlib.sha256()
+    for k in _ARRAYS:
+        a = np.ascontiguousarray(getattr(s, k))
+        h.update(k.encode())
+        h.update(str(a.dtype).encode())
+        h.update(str(a.shape).encode())
+        h.update(a.tobytes())
+    h.update(repr((float(s.coulomb_c), int(s.exclusions), float(s.scale14))).encode())
+    return h.hexdigest()
+
+
+def save_npz(s: System, path: str) -> str:
+    """Write the system's arrays to an .npz file; returns its digest."""
+    np.savez(path, **{k: getattr(s, k) for k in _ARRAYS}, coulomb_c=s.coulomb_c,
+             exclusions=s.exclusions, scale14=s.scale14, seed=s.seed)
+    return digest(s)
+
+
+def load_npz(path: str) -> System:
+    """Read a system written by save_npz."""
+    d = np.load(path)
+    kw = {k: d[k] for k in _ARRAYS}
+    return System(x_ref=d["x"].copy(), coulomb_c=float(d["coulomb_c"]), exclusions=int(d["exclusions"]),
+                  scale14=float(d["scale14"]), seed=int(d["seed"]), **kw)
