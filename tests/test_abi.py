@@ -78,3 +78,16 @@ def test_create_rejects_bad_topology_on_host(built):
     assert b"out of range" in ffmin.lib().ffmin_last_error(None)
     st = ffmin.lib().ffmin_create(C.byref(top), 0, 0, None, C.byref(h))
     assert st == ffmin.FFMIN_ERR_INVALID_ARG
+
+
+def test_option_defaults_agree_with_the_oracle(built, oracle_mod):
+    # the library's and the oracle's defaults are the readings of the paper
+    # (first step 0.1 A, k+ = 2, k- = 0.5, eps_h = 1e-10, LS_PAR K = 2 with
+    # G0, m = 10, |grad|_inf < 0.1); both sides set them independently
+    from paper_1810_03358_gb300 import ffmin
+    g = ffmin.ffmin_options_default()
+    o, _ = oracle_mod.options()
+    for k in ("method", "cg_variant", "ls", "lbfgs_m", "gtol_inf", "max_iter", "max_evals", "h0", "k_plus",
+              "k_minus", "eps_h", "ls_par_K", "ls_par_g0", "gradfree_delta", "gradfree_parts"):
+        assert getattr(g, k) == getattr(o, k), k
+    assert (g.h0, g.k_plus, g.k_minus, g.ls_par_K, g.lbfgs_m, g.gtol_inf) == (0.1, 2.0, 0.5, 2, 10, 0.1)
