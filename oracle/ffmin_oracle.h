@@ -63,6 +63,13 @@ int orc_energy_terms(const orc_ff *ff, const double *x, double *grad, orc_terms 
  * moves (pair terms with i plus bonded terms containing i). */
 double orc_row_energy(const orc_ff *ff, const double *x, int32_t i, const double p[3]);
 
+/* The same with the Coulomb terms of every atom at least r_far from x_i
+ * replaced by their first-order Taylor expansion about x_i (Section 3's
+ * amortised construction for the gradient-free moves); r_far = +inf gives
+ * orc_row_energy. */
+double orc_row_energy_taylor(const orc_ff *ff, const double *x, int32_t i, const double p[3],
+                             double r_far);
+
 /* Gradient of E with respect to atom i alone (g3[3]); pair row plus the
  * bonded terms that contain atom i. */
 int orc_atom_gradient(const orc_ff *ff, const double *x, int32_t i, double *g3);
@@ -105,6 +112,7 @@ typedef struct {
      * than gradfree_margin A to a slab boundary stay put in that epoch */
     int32_t gradfree_parts;
     double gradfree_margin;
+    double gradfree_taylor_r;  /* > 0: moves use orc_row_energy_taylor with this r_far */
     const double *precond_d;   /* optional fixed per-variable H0 diagonal [n] (L-BFGS) */
     const double *mlp_w;       /* optional network [ORC_MLP_NW]: H0 diagonal per iteration (force field) */
     double ogm_step;           /* OGM: fixed step 1/L instead of the line search when > 0 (tests) */

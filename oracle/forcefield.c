@@ -291,21 +291,9 @@ int orc_energy_terms(const orc_ff *ff, const double *x, double *grad, orc_terms 
 }
 
 /* Part of E that depends on atom i, with atom i at p. */
-double orc_row_energy(const orc_ff *ff, const double *x, int32_t i, const double p[3]) {
-    const int n = ff->n_atoms;
-    double e = 0.0;
-    int32_t m_sc;
-    pscale_t *sc = scale_table(ff, &m_sc);
-    for (int j = 0; j < n; j++) {
-        if (j == i) continue;
-        const double s = pair_scale(ff, sc, m_sc, i, j);
-        if (s == 0.0) continue;
-        double d[3], ec, ev, f;
-        sub3(p, x + 3 * j, d);
-        e += s * pair_term(ff->coulomb_c, ff->charge[i], ff->charge[j], ff->sigma[i], ff->sigma[j],
-                           ff->epsilon[i], ff->epsilon[j], d, &ec, &ev, &f);
-    }
-    free(sc);
+/* e plus every bonded term containing atom i, with atom i at p, added one
+ * at a time (bonds, angles, dihedrals) */
+static double add_row_bonded(const orc_ff *ff, const double *x, int32_t i, const double p[3], double e) {
 #define POS(a) ((a) == i ? p : x + 3 * (a))
     for (int b = 0; b < ff->n_bonds; b++) {
         int a0 = ff->bond_idx[2 * b], a1 = ff->bond_idx[2 * b + 1];
@@ -326,6 +314,64 @@ double orc_row_energy(const orc_ff *ff, const double *x, int32_t i, const double
     }
 #undef POS
     return e;
+}
+
+double orc_row_energy(const orc_ff *ff, const double *x, int32_t i, const double p[3]) {
+    const int n = ff->n_atoms;
+    double e = 0.0;
+    int32_t m_sc;
+    pscale_t *sc = scale_table(ff, &m_sc);
+    for (int j = 0; j < n; j++) {
+        if (j == i) continue;
+        const double s = pair_scale(ff, sc, m_sc, i, j);
+        if (s == 0.0) continue;
+        double d[3], ec, ev, f;
+        sub3(p, x + 3 * j, d);
+        e += s * pair_term(ff->coulomb_c, ff->charge[i], ff->charge[j], ff->sigma[i], ff->sigma[j],
+                           ff->epsilon[i], ff->epsilon[j], d, &ec, &ev, &f);
+    }
+    free(sc);
+    return add_row_bonded(ff, x, i, p, e);
+}
+
+/* The row energy with the far Coulomb terms linearised (Section 3's
+ * construction for the gradient-free moves): for every atom j at least r_far
+ * from the atom's current position x_i, the Coulomb term at p is replaced by
+ * its first-order Taylor expansion about x_i,
+ *     e_c(x_i) + grad_i e_c(x_i) . (p - x_i) = e_c0 (1 - d0 . (p - x_i) / r0^2),
+ * d0 = x_i - x_j, r0 = |d0|; the Lennard-Jones terms, the near Coulomb terms
+ * and the bonded terms stay exact.  r_far = +inf gives orc_row_energy. */
+double orc_row_energy_taylor(const orc_ff *ff, const double *x, int32_t i, const double p[3],
+                             double r_far) {
+    const int n = ff->n_atoms;
+    double e = 0.0, delta[3];
+    sub3(p, x + 3 * i, delta);
+    int32_t m_sc;
+    pscale_t *sc = scale_table(ff, &m_sc);
+    for (int j = 0; j < n; j++) {
+        if (j == i) continue;
+        const double s = pair_scale(ff, sc, m_sc, i, j);
+        if (s == 0.0) continue;
+        double d0[3], ec, ev, f;
+        sub3(x + 3 * i, x + 3 * j, d0);
+        const double r02 = dot3(d0, d0);
+        if (r02 >= r_far * r_far) {
+            double d[3], ec_p;
+            sub3(p, x + 3 * j, d);
+            pair_term(ff->coulomb_c, ff->charge[i], ff->charge[j], ff->sigma[i], ff->sigma[j],
+                      ff->epsilon[i], ff->epsilon[j], d, &ec_p, &ev, &f);
+            pair_term(ff->coulomb_c, ff->charge[i], ff->charge[j], ff->sigma[i], ff->sigma[j],
+                      ff->epsilon[i], ff->epsilon[j], d0, &ec, &f, &f);
+            e += s * (ev + ec * (1.0 - dot3(d0, delta) / r02));
+        } else {
+            double d[3];
+            sub3(p, x + 3 * j, d);
+            e += s * pair_term(ff->coulomb_c, ff->charge[i], ff->charge[j], ff->sigma[i], ff->sigma[j],
+                               ff->epsilon[i], ff->epsilon[j], d, &ec, &ev, &f);
+        }
+    }
+    free(sc);
+    return add_row_bonded(ff, x, i, p, e);
 }
 
 int32_t orc_neighbour_count(const orc_ff *ff, const double *x, int32_t i, double rc) {

@@ -584,7 +584,11 @@ static double ff_fg(void *ctx, const double *x, double *g, int32_t *status) {
 /* one gradient-free move of atom i in x: the best of 7 axis points (current,
  * +-delta on x, y, z) and the vertex of the per-axis parabolas (8 row
  * energies, Section 3) */
-static void parab_move(const orc_ff *ff, double *x, int32_t i, double dl) {
+static double move_row(const orc_ff *ff, const double *x, int32_t i, const double *p, double r_far) {
+    return r_far > 0.0 ? orc_row_energy_taylor(ff, x, i, p, r_far) : orc_row_energy(ff, x, i, p);
+}
+
+static void parab_move(const orc_ff *ff, double *x, int32_t i, double dl, double r_far) {
     double p[8][3], fv[8];
     for (int c = 0; c < 8; c++)
         for (int a = 0; a < 3; a++) p[c][a] = x[3 * i + a];
@@ -592,14 +596,14 @@ static void parab_move(const orc_ff *ff, double *x, int32_t i, double dl) {
         p[1 + 2 * a][a] += dl; /* +delta */
         p[2 + 2 * a][a] -= dl; /* -delta */
     }
-    for (int c = 0; c < 7; c++) fv[c] = orc_row_energy(ff, x, i, p[c]);
+    for (int c = 0; c < 7; c++) fv[c] = move_row(ff, x, i, p[c], r_far);
     for (int a = 0; a < 3; a++) {
         double fp = fv[1 + 2 * a], fm = fv[2 + 2 * a];
         double curv = fm - 2.0 * fv[0] + fp;
         double ts = curv > 0.0 ? dl * (fm - fp) / (2.0 * curv) : 0.0;
         p[7][a] = x[3 * i + a] + ts;
     }
-    fv[7] = orc_row_energy(ff, x, i, p[7]);
+    fv[7] = move_row(ff, x, i, p[7], r_far);
     int best = 0;
     for (int c = 1; c < 8; c++)
         if (fv[c] < fv[best]) best = c;
@@ -624,7 +628,7 @@ static int parab(const orc_ff *ff, double *x, const orc_options *op, orc_result 
             for (int32_t sweep = 0; sweep < n; sweep++) {
                 if (moves >= op->max_iter) { status = ORC_MAX_ITER; break; }
                 int32_t i = orc_pick_atom(op->seed, (uint64_t)moves, n);
-                parab_move(ff, x, i, dl);
+                parab_move(ff, x, i, dl, op->gradfree_taylor_r);
                 ne += 8;
                 moves++;
             }
@@ -766,7 +770,7 @@ static int parab_epochs(const orc_ff *ff, double *x, const orc_options *op, orc_
                 memcpy(xv, xs, nb);
                 for (int32_t m = 0; m < allowed; m++) {
                     const uint64_t k = ((uint64_t)q << 40) + e * (uint64_t)n + (uint64_t)m;
-                    parab_move(ff, xv, list[orc_pick_atom(op->seed, k, m_q)], dl);
+                    parab_move(ff, xv, list[orc_pick_atom(op->seed, k, m_q)], dl, op->gradfree_taylor_r);
                     ne += 8;
                 }
                 for (int32_t a = 0; a < n; a++)

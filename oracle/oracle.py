@@ -47,7 +47,7 @@ class _Opt(C.Structure):
                 ("k_plus", C.c_double), ("k_minus", C.c_double), ("eps_h", C.c_double),
                 ("ls_par_K", C.c_int32), ("ls_par_g0", C.c_int32),
                 ("gradfree_delta", C.c_double), ("seed", C.c_uint64), ("gradfree_parts", C.c_int32),
-                ("gradfree_margin", C.c_double), ("precond_d", _dp),
+                ("gradfree_margin", C.c_double), ("gradfree_taylor_r", C.c_double), ("precond_d", _dp),
                 ("mlp_w", _dp), ("ogm_step", C.c_double)]
 
 
@@ -70,6 +70,8 @@ def lib():
         L.orc_energy_terms.restype = C.c_int
         L.orc_row_energy.argtypes = [C.POINTER(_FF), _dp, C.c_int32, _dp]
         L.orc_row_energy.restype = C.c_double
+        L.orc_row_energy_taylor.argtypes = [C.POINTER(_FF), _dp, C.c_int32, _dp, C.c_double]
+        L.orc_row_energy_taylor.restype = C.c_double
         L.orc_atom_gradient.argtypes = [C.POINTER(_FF), _dp, C.c_int32, _dp]
         L.orc_atom_gradient.restype = C.c_int
         L.orc_neighbour_count.argtypes = [C.POINTER(_FF), _dp, C.c_int32, C.c_double]
@@ -159,6 +161,14 @@ def row_energy(s, x, i, p):
     xx = _f64(x).reshape(-1)
     pp = _f64(p).reshape(3)
     return lib().orc_row_energy(C.byref(f.s), _dptr(xx), int(i), _dptr(pp))
+
+
+def row_energy_taylor(s, x, i, p, r_far):
+    """Row energy of atom i at p with the far Coulomb terms linearised."""
+    f = _ff(s)
+    xx = _f64(x).reshape(-1)
+    pp = _f64(p).reshape(3)
+    return lib().orc_row_energy_taylor(C.byref(f.s), _dptr(xx), int(i), _dptr(pp), float(r_far))
 
 
 def atom_gradient(s, x, i):
