@@ -95,7 +95,7 @@ double orc_ls_par(orc_line_fn phi, void *ctx, double f_star, double slope, doubl
                   int32_t K, int32_t g0, double k_plus, double *f_out, int32_t *n_evals);
 
 /* Minimizer options / results. */
-enum { ORC_GD = 0, ORC_FGM = 1, ORC_CG = 2, ORC_LBFGS = 3, ORC_GRADFREE = 4, ORC_OGM = 5 };
+enum { ORC_GD = 0, ORC_FGM = 1, ORC_CG = 2, ORC_LBFGS = 3, ORC_GRADFREE = 4, ORC_OGM = 5, ORC_HB = 6 };
 enum { ORC_CG_PRP = 0, ORC_CG_HS, ORC_CG_FR, ORC_CG_PRP_PLUS, ORC_CG_CD, ORC_CG_LS, ORC_CG_DY };
 enum { ORC_LS_DEFAULT = 0, ORC_LS_H = 1, ORC_LS_PAR = 2 };
 
@@ -116,6 +116,7 @@ typedef struct {
     const double *precond_d;   /* optional fixed per-variable H0 diagonal [n] (L-BFGS) */
     const double *mlp_w;       /* optional network [ORC_MLP_NW]: H0 diagonal per iteration (force field) */
     double ogm_step;           /* OGM: fixed step 1/L instead of the line search when > 0 (tests) */
+    double hb_alpha, hb_beta;  /* heavy ball (Eq. 8): constant step alpha > 0 and momentum beta >= 0 */
 } orc_options;
 
 typedef struct {

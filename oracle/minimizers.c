@@ -9,6 +9,7 @@
  *   CG      Algorithm 2, beta variants of Section 4 / Section 5.1
  *   L-BFGS  Algorithms 3 and 4 (Section 5.1)
  *   parab   gradient-free random-atom moves (Section 3)
+ *   HB      the heavy-ball method of Section 4 (Eq. 8) with constant alpha, beta
  *   OGM     the optimized gradient method of Section 4 (Eq. 11) with its
  *           step 1/L replaced by a line search over h (the variant the
  *           paper gives right after Eq. 13)
@@ -427,6 +428,31 @@ int orc_minimize(int32_t n, orc_fg_fn fg, void *ctx, double *x, const orc_option
                 result_ginf = infnorm(n, g);
             }
         }
+        goto done;
+    }
+
+    if (method == ORC_HB) {
+        /* Eq. 8: x^{k+1} = x^k - alpha grad f(x^k) + beta (x^k - x^{k-1}),
+         * x^{-1} = x^0, formed as fma(beta, x^k - x^{k-1}, fma(-alpha, g, x^k)) */
+        if (!(op->hb_alpha > 0.0) || !(op->hb_beta >= 0.0)) { status = ORC_BAD_ARG; goto done; }
+        memcpy(xp, x, nb);
+        for (;;) {
+            if (ginf < op->gtol_inf) { status = ORC_OK; break; }
+            if (CAP_HIT(it, o)) { status = ORC_MAX_ITER; break; }
+            for (int32_t k = 0; k < n; k++)
+                xn[k] = fma(op->hb_beta, x[k] - xp[k], fma(-op->hb_alpha, g[k], x[k]));
+            double fn = obj_eg(&o, xn, gn);
+            memcpy(xp, x, nb);
+            memcpy(x, xn, nb);
+            memcpy(g, gn, nb);
+            f = fn;
+            ginf = infnorm(n, g);
+            if (o.status) { status = o.status; break; }
+            it++;
+            trace_add(fn, op->hb_alpha, 0.0, op->hb_beta);
+        }
+        result_f = f;
+        result_ginf = ginf;
         goto done;
     }
 

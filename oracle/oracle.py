@@ -16,7 +16,7 @@ from . import build as _build
 
 _lib = None
 
-GD, FGM, CG, LBFGS, GRADFREE, OGM = 0, 1, 2, 3, 4, 5
+GD, FGM, CG, LBFGS, GRADFREE, OGM, HB = 0, 1, 2, 3, 4, 5, 6
 CG_PRP, CG_HS, CG_FR, CG_PRP_PLUS, CG_CD, CG_LS, CG_DY = range(7)
 LS_DEFAULT, LS_H, LS_PAR = 0, 1, 2
 STATUS = {0: "ok", 1: "nonfinite", 2: "linesearch", 3: "max_iter", 4: "bad_arg"}
@@ -48,7 +48,8 @@ class _Opt(C.Structure):
                 ("ls_par_K", C.c_int32), ("ls_par_g0", C.c_int32),
                 ("gradfree_delta", C.c_double), ("seed", C.c_uint64), ("gradfree_parts", C.c_int32),
                 ("gradfree_margin", C.c_double), ("gradfree_taylor_r", C.c_double), ("precond_d", _dp),
-                ("mlp_w", _dp), ("ogm_step", C.c_double)]
+                ("mlp_w", _dp), ("ogm_step", C.c_double), ("hb_alpha", C.c_double),
+                ("hb_beta", C.c_double)]
 
 
 class _Res(C.Structure):
