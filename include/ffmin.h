@@ -49,7 +49,8 @@ typedef enum {
     FFMIN_ERR_OOM = 7
 } ffmin_status;
 
-/* GD: adaptive steepest descent (Section 3, Eq. 4); FGM: Algorithm 1; CG:
+/* GD: adaptive steepest descent (Section 3, Eq. 4); FGM: Algorithm 1 (see
+ * options.fgm_restart); CG:
  * Algorithm 2; LBFGS: Algorithms 3-4; GRADFREE: random-atom parabolic moves
  * (Section 3); OGM: the optimized gradient method of Section 4 (Eq. 11) with
  * the step 1/L replaced by a line search from y (LS_PAR with G0 by default),
@@ -127,7 +128,14 @@ typedef struct {
     int32_t gradfree_parts;
     double gradfree_margin;
     int32_t use_learned_precond; /* L-BFGS: scale H0 by the learned per-atom diagonal */
-    int32_t max_ticks;       /* safety bound on device evaluation rounds; 0 -> max_evals + 64 */
+    /* Bound on device evaluation rounds (each round evaluates at most one E
+     * or E + grad per system; rounds run in groups of 8); 0 -> max_evals + 64.
+     * A system still running when it is reached stops with
+     * FFMIN_ERR_TIMEOUT: x then holds its last accepted point (FGM: its best
+     * point), energy that point's energy (from the pair terms of the current
+     * precision phase) and grad_inf its |grad|_inf (NaN for FGM when that
+     * gradient was never evaluated). */
+    int32_t max_ticks;
     /* L-BFGS trajectory recording (training data of the preconditioner):
      * when record_dev != NULL, after every record_every-th accepted step k
      * (slot k / record_every - 1 < record_slots) every atom i of every system
@@ -135,6 +143,12 @@ typedef struct {
      * record_dev[(slot * total_atoms + i) * 4 + 0..3] (device, FP64). */
     double *record_dev;
     int32_t record_every, record_slots;
+    /* FGM: 0 (default) runs Algorithm 1 as printed (non-monotone, no
+     * momentum restart; the best point is returned); 1 adds the
+     * function-value adaptive restart of O'Donoghue and Candes (theta <- 1,
+     * momentum dropped whenever f(x^{k+1}) > f(x^k)), which Algorithm 1 does
+     * not have. */
+    int32_t fgm_restart;
 } ffmin_options;
 
 typedef struct {
@@ -182,6 +196,19 @@ ffmin_status ffmin_energy_grad(ffmin_system *sys, const double *x_dev, double *e
  * copies the gradient back to g_host (pass NULL to skip it). */
 ffmin_status ffmin_energy_grad_host(ffmin_system *sys, const double *x_host, double *e_host,
                                     double *g_host);
+
+/* Energy change of a line-search trial, evaluated the way the minimizers
+ * evaluate it (Section 5.2's searches compare f(x + h r) with f(x)):
+ * de_host[b] = E_b(x + h r) - E_b(x) for every system, x_dev and r_dev
+ * [3 * total atoms] (device, FP64; r is used as given, not normalised).
+ * FFMIN_FP64: the difference of two FP64 energies.  FFMIN_MIXED: x is
+ * evaluated with E + grad (FP32 pair terms), then the trial with every pair
+ * term taken as an exact FP32 difference from x (the form of every MIXED
+ * energy-only trial) and the bonded terms in FP64.  Errors: INVALID_ARG,
+ * NONFINITE (coincident atoms at x or at the trial).  Synchronizes the
+ * stream.  A diagnostic of the trials' accuracy. */
+ffmin_status ffmin_energy_delta(ffmin_system *sys, const double *x_dev, const double *r_dev, double h,
+                                double *de_host);
 
 /* Minimize every system of the batch from x_dev (device, in/out): on
  * return x_dev holds each system's result and results[n_sys] its record.
@@ -266,15 +293,20 @@ ffmin_status ffmin_last_stats(const ffmin_system *sys, int64_t *ticks,
  * and its gradient.  All buffers are the caller's device memory:
  *   x_dev [3N] xyz per atom; charge_dev, sigma_dev, epsilon_dev [N];
  *   g_dev [3N] gradient out; e_dev [1] energy out.
- * coulomb_c: 0 -> 332.0716 kcal*A/(mol*e^2).  Work is enqueued on
- * cuda_stream (NULL = legacy default stream); nothing is synchronised.
+ * coulomb_c: 0 -> 332.0716 kcal*A/(mol*e^2); negative or non-finite ->
+ * FFMIN_ERR_INVALID_ARG.  Work is enqueued on cuda_stream (NULL = legacy
+ * default stream); the call then synchronises that stream to read its
+ * status: FFMIN_ERR_NONFINITE when the energy or a gradient component is not
+ * finite (two coincident atoms), else FFMIN_OK.
  * Scratch: a fixed device array inside the library (about 2 MB, held by
  * every GPU that loads the library until the process exits); n_atoms above
  * 8192 returns FFMIN_ERR_INVALID_ARG.  The first call on each device looks
- * up the array's device address, so make that first call before any stream
- * capture.  Every call uses the same array: calls that overlap on the GPU
- * (concurrent streams) race; serialise them.  No cudaMalloc or cudaFree is
- * ever called. */
+ * up the array's device address in the device's primary context and keeps
+ * it, so make that first call before any stream capture, and do not use
+ * the entry point after cudaDeviceReset or from a non-primary context.
+ * Every call uses the same array: calls that overlap on the GPU (concurrent
+ * streams) race; serialise them.  No cudaMalloc or cudaFree is ever
+ * called. */
 ffmin_status ffmin_pair_energy_grad_noalloc(const double *x_dev, const double *charge_dev,
                                             const double *sigma_dev, const double *epsilon_dev,
                                             int32_t n_atoms, double coulomb_c, double *g_dev,

@@ -58,6 +58,13 @@ enum { ORC_OK = 0, ORC_NONFINITE = 1, ORC_LINESEARCH = 2, ORC_MAX_ITER = 3, ORC_
  * not finite. */
 int orc_energy_terms(const orc_ff *ff, const double *x, double *grad, orc_terms *out);
 
+/* E(xp) - E(x) summed term by term (each term at xp minus itself at x),
+ * *sum_abs = sum over terms of |difference|: the definition of a line-search
+ * trial's energy change.  Pairs (i, j), i < j, with i in [i0, i1); the
+ * bonded terms only when i0 == 0 (callers may split the rows). */
+int orc_energy_delta(const orc_ff *ff, const double *x, const double *xp, int32_t i0, int32_t i1,
+                     double *delta, double *sum_abs);
+
 /* Energy of every term that contains atom i, with atom i placed at p[3]
  * and every other atom at x: the part of E that changes when only atom i
  * moves (pair terms with i plus bonded terms containing i). */
@@ -117,6 +124,8 @@ typedef struct {
     const double *mlp_w;       /* optional network [ORC_MLP_NW]: H0 diagonal per iteration (force field) */
     double ogm_step;           /* OGM: fixed step 1/L instead of the line search when > 0 (tests) */
     double hb_alpha, hb_beta;  /* heavy ball (Eq. 8): constant step alpha > 0 and momentum beta >= 0 */
+    int32_t fgm_restart;       /* FGM: 1 adds the function-value momentum restart (not in Algorithm 1) */
+    double fgm_step;           /* FGM: fixed step 1/L instead of the line search when > 0 (tests) */
 } orc_options;
 
 typedef struct {

@@ -290,6 +290,74 @@ int orc_energy_terms(const orc_ff *ff, const double *x, double *grad, orc_terms 
     return status;
 }
 
+/* E(xp) - E(x) as a sum of per-term differences (every Section 2 term at
+ * xp minus the same term at x), with the sum of |difference| over the terms.
+ * Pairs (i, j), i < j, with i in [i0, i1) (so that independent callers can
+ * split the rows); the bonded terms only when i0 == 0. */
+int orc_energy_delta(const orc_ff *ff, const double *x, const double *xp, int32_t i0, int32_t i1,
+                     double *delta, double *sum_abs) {
+    const int n = ff->n_atoms;
+    int status = ORC_OK;
+    double dsum = 0.0, asum = 0.0;
+    int32_t m_sc;
+    pscale_t *sc = scale_table(ff, &m_sc);
+    if (i0 < 0) i0 = 0;
+    if (i1 > n) i1 = n;
+    for (int i = i0; i < i1; i++) {
+        for (int j = i + 1; j < n; j++) {
+            double d0[3], d1[3];
+            sub3(x + 3 * i, x + 3 * j, d0);
+            sub3(xp + 3 * i, xp + 3 * j, d1);
+            if (dot3(d0, d0) == 0.0 || dot3(d1, d1) == 0.0) { status = ORC_NONFINITE; continue; }
+            const double s = pair_scale(ff, sc, m_sc, i, j);
+            if (s == 0.0) continue;
+            double ec, ev, f;
+            const double e0 = pair_term(ff->coulomb_c, ff->charge[i], ff->charge[j], ff->sigma[i],
+                                        ff->sigma[j], ff->epsilon[i], ff->epsilon[j], d0, &ec, &ev, &f);
+            const double e1 = pair_term(ff->coulomb_c, ff->charge[i], ff->charge[j], ff->sigma[i],
+                                        ff->sigma[j], ff->epsilon[i], ff->epsilon[j], d1, &ec, &ev, &f);
+            const double de = s * (e1 - e0);
+            dsum += de;
+            asum += fabs(de);
+        }
+    }
+    free(sc);
+    if (i0 == 0) {
+        for (int b = 0; b < ff->n_bonds; b++) {
+            int i = ff->bond_idx[2 * b], j = ff->bond_idx[2 * b + 1];
+            const double de = bond_term(xp + 3 * i, xp + 3 * j, ff->bond_k[b], ff->bond_r0[b], NULL, NULL) -
+                              bond_term(x + 3 * i, x + 3 * j, ff->bond_k[b], ff->bond_r0[b], NULL, NULL);
+            dsum += de;
+            asum += fabs(de);
+        }
+        for (int b = 0; b < ff->n_angles; b++) {
+            const int32_t *q = ff->angle_idx + 3 * b;
+            const double de =
+                angle_term(xp + 3 * q[0], xp + 3 * q[1], xp + 3 * q[2], ff->angle_k[b], ff->angle_theta0[b],
+                           NULL, NULL, NULL) -
+                angle_term(x + 3 * q[0], x + 3 * q[1], x + 3 * q[2], ff->angle_k[b], ff->angle_theta0[b],
+                           NULL, NULL, NULL);
+            dsum += de;
+            asum += fabs(de);
+        }
+        for (int b = 0; b < ff->n_dihedrals; b++) {
+            const int32_t *q = ff->dihedral_idx + 4 * b;
+            const double *v = ff->dihedral_v + 4 * b;
+            const double de =
+                dihedral_term(xp + 3 * q[0], xp + 3 * q[1], xp + 3 * q[2], xp + 3 * q[3], v, NULL, NULL, NULL,
+                              NULL, NULL) -
+                dihedral_term(x + 3 * q[0], x + 3 * q[1], x + 3 * q[2], x + 3 * q[3], v, NULL, NULL, NULL,
+                              NULL, NULL);
+            dsum += de;
+            asum += fabs(de);
+        }
+    }
+    if (!isfinite(dsum)) status = ORC_NONFINITE;
+    *delta = dsum;
+    *sum_abs = asum;
+    return status;
+}
+
 /* Part of E that depends on atom i, with atom i at p. */
 /* e plus every bonded term containing atom i, with atom i at p, added one
  * at a time (bonds, angles, dihedrals) */

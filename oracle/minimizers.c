@@ -31,10 +31,12 @@
  *    pairs with <s,y> <= 0;
  *  - CG: beta uses the previous unnormalised direction; restart every
  *    cg_restart_every iterations and whenever <g+, r+> >= 0;
- *  - FGM: stop when |grad f(w)|_inf < tol and return the better of the best
- *    iterate and w; the momentum is reset (theta <- 1, x^{k-1} <- x^{k+1})
- *    whenever f(x^{k+1}) > f(x^k), the function-value adaptive restart of
- *    O'Donoghue and Candes that Section 4 cites for restarting.
+ *  - FGM: Algorithm 1 as printed (non-monotone, no momentum restart; the
+ *    best point x_* is what is returned); stop when |grad f(w)|_inf < tol
+ *    and return the better of the best iterate and w.  Option fgm_restart
+ *    adds the function-value adaptive restart of O'Donoghue and Candes
+ *    (theta <- 1, x^{k-1} <- x^{k+1} whenever f(x^{k+1}) > f(x^k)), which
+ *    the paper does not use in Algorithm 1.
  *  - OGM: t_0 = 1; the gradient is evaluated at y (the base of the line
  *    search, which takes LS_PAR with G0 by default, steps of either sign);
  *    stop when |grad f(x^k)|_inf < tol; no momentum restart (the method is
@@ -388,8 +390,16 @@ int orc_minimize(int32_t n, orc_fg_fn fg, void *ctx, double *x, const orc_option
             for (int32_t k = 0; k < n; k++) r[k] = -gw[k];
             normalise(n, r, rhat);
             int32_t ne = 0;
-            double fnew;
-            double h = line_search(op, method, &o, w, rhat, xt, fw, dotn(n, gw, rhat), h0, &fnew, &ne);
+            double fnew, h;
+            if (op->fgm_step > 0.0) {
+                /* fixed step 1/L (tests): x^{k+1} = w^k - grad f(w^k) / L, i.e.
+                 * h = |grad f(w^k)|_2 / L along r^k; f(x^{k+1}) for the best point */
+                line_t l = {&o, w, rhat, xt};
+                h = op->fgm_step * sqrt(dotn(n, gw, gw));
+                fnew = line_phi(&l, h);
+            } else {
+                h = line_search(op, method, &o, w, rhat, xt, fw, dotn(n, gw, rhat), h0, &fnew, &ne);
+            }
             if (h == 0.0) {
                 lsf++;
                 if (fresh) { status = ORC_LINESEARCH; break; }
@@ -405,8 +415,9 @@ int orc_minimize(int32_t n, orc_fg_fn fg, void *ctx, double *x, const orc_option
             memcpy(xp, x, nb);
             for (int32_t k = 0; k < n; k++) x[k] = fma(h, rhat[k], w[k]);
             trace_add(fnew, h, th, beta);
-            if (fnew > fx) {
-                /* adaptive restart (function scheme): the new iterate is worse
+            if (op->fgm_restart && fnew > fx) {
+                /* optional adaptive restart (function scheme of O'Donoghue and
+                 * Candes; not part of Algorithm 1): the new iterate is worse
                  * than the previous one, so the momentum is dropped */
                 th_prev = 1.0;
                 memcpy(xp, x, nb);
@@ -442,12 +453,13 @@ int orc_minimize(int32_t n, orc_fg_fn fg, void *ctx, double *x, const orc_option
             for (int32_t k = 0; k < n; k++)
                 xn[k] = fma(op->hb_beta, x[k] - xp[k], fma(-op->hb_alpha, g[k], x[k]));
             double fn = obj_eg(&o, xn, gn);
+            /* a failed evaluation ends the run at the last good iterate */
+            if (o.status) { status = o.status; break; }
             memcpy(xp, x, nb);
             memcpy(x, xn, nb);
             memcpy(g, gn, nb);
             f = fn;
             ginf = infnorm(n, g);
-            if (o.status) { status = o.status; break; }
             it++;
             trace_add(fn, op->hb_alpha, 0.0, op->hb_beta);
         }

@@ -49,7 +49,7 @@ class _Opt(C.Structure):
                 ("gradfree_delta", C.c_double), ("seed", C.c_uint64), ("gradfree_parts", C.c_int32),
                 ("gradfree_margin", C.c_double), ("gradfree_taylor_r", C.c_double), ("precond_d", _dp),
                 ("mlp_w", _dp), ("ogm_step", C.c_double), ("hb_alpha", C.c_double),
-                ("hb_beta", C.c_double)]
+                ("hb_beta", C.c_double), ("fgm_restart", C.c_int32), ("fgm_step", C.c_double)]
 
 
 class _Res(C.Structure):
@@ -69,6 +69,8 @@ def lib():
         L = C.CDLL(path)
         L.orc_energy_terms.argtypes = [C.POINTER(_FF), _dp, _dp, C.POINTER(_Terms)]
         L.orc_energy_terms.restype = C.c_int
+        L.orc_energy_delta.argtypes = [C.POINTER(_FF), _dp, _dp, C.c_int32, C.c_int32, _dp, _dp]
+        L.orc_energy_delta.restype = C.c_int
         L.orc_row_energy.argtypes = [C.POINTER(_FF), _dp, C.c_int32, _dp]
         L.orc_row_energy.restype = C.c_double
         L.orc_row_energy_taylor.argtypes = [C.POINTER(_FF), _dp, C.c_int32, _dp, C.c_double]
@@ -155,6 +157,20 @@ def energy(s, x):
 def energy_grad(s, x):
     d, st, g = energy_terms(s, x, grad=True)
     return d["total"], g
+
+
+def energy_delta(s, x, xp, rows=None):
+    """(E(xp) - E(x) summed term by term, sum of |term differences|, status);
+    rows = (i0, i1) restricts the pairs to rows i0 <= i < i1 (bonded terms
+    only with i0 == 0)."""
+    f = _ff(s)
+    a = _f64(x).reshape(-1)
+    b = _f64(xp).reshape(-1)
+    i0, i1 = rows if rows is not None else (0, f.n)
+    d = C.c_double()
+    sa = C.c_double()
+    st = lib().orc_energy_delta(C.byref(f.s), _dptr(a), _dptr(b), int(i0), int(i1), C.byref(d), C.byref(sa))
+    return d.value, sa.value, st
 
 
 def row_energy(s, x, i, p):

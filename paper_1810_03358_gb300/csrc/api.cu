@@ -223,6 +223,7 @@ void ffmin_options_default(ffmin_options *o) {
     o->record_dev = nullptr;
     o->record_every = 0;
     o->record_slots = 0;
+    o->fgm_restart = 0;
 }
 
 const char *ffmin_status_string(ffmin_status s) {
@@ -659,8 +660,12 @@ static ffmin_status ensure_graph(ffmin_system *sys) {
     return FFMIN_OK;
 }
 
-// one evaluation (E or EG) of every system at the vector in `slot`
-static ffmin_status eval_slot(ffmin_system *sys, int slot, int kind) {
+// one evaluation (E or EG) of every system at the vector in `slot`, or at
+// slot + h * dir when dir >= 0; delta = 1 takes a MIXED energy-only trial
+// the way a line search does: pair terms as exact FP32 differences from the
+// pair energy of the last E + grad evaluation (at `slot`), bonded terms in FP64
+static ffmin_status eval_slot(ffmin_system *sys, int slot, int kind, int dir = -1, double h = 0.0,
+                              int delta = 0) {
     const Ctx &c = sys->c;
     for (int b = 0; b < sys->n_sys; b++) {
         SysState &S = sys->hst[b];
@@ -670,12 +675,13 @@ static ffmin_status eval_slot(ffmin_system *sys, int slot, int kind) {
         S.dir[0].on = S.dir[1].on = 0;
         S.ev_kind = kind;
         S.ev_base = slot;
-        S.ev_dir = -1;
-        S.ev_h = 0.0;
+        S.ev_dir = dir;
+        S.ev_h = h;
         S.ev_scale = 1.0;
-        S.ev_delta = 0;
         S.ne = S.neg = 0;
         S.mode = sys->prec == FFMIN_MIXED ? 0 : 1;
+        S.ev_delta = (delta && S.mode == 0 && kind == EV_E && dir >= 0) ? 1 : 0;
+        S.epair_base = S.epair_last;
     }
     ffmin_status st = upload_states(sys);
     if (st != FFMIN_OK) return st;
@@ -750,6 +756,31 @@ ffmin_status ffmin_energy_grad_host(ffmin_system *sys, const double *x_host, dou
     return st != FFMIN_OK ? st : res;
 }
 
+ffmin_status ffmin_energy_delta(ffmin_system *sys, const double *x_dev, const double *r_dev, double h,
+                                double *de_host) {
+    ffmin_status st = enter(sys);
+    if (st != FFMIN_OK) return st;
+    if (!x_dev || !r_dev || !de_host || !std::isfinite(h)) return fail(sys, FFMIN_ERR_INVALID_ARG, "bad argument");
+    const size_t bytes = sizeof(double) * 3 * sys->n_atoms;
+    CK(cudaMemcpyAsync(vslot(sys->c, V_XIN), x_dev, bytes, cudaMemcpyDeviceToDevice, sys->stream));
+    CK(cudaMemcpyAsync(vslot(sys->c, V_R), r_dev, bytes, cudaMemcpyDeviceToDevice, sys->stream));
+    // the base of a line search is an E + grad evaluation
+    if ((st = eval_slot(sys, V_XIN, EV_EG)) != FFMIN_OK) return st;
+    ffmin_status res = FFMIN_OK;
+    std::vector<double> base(sys->n_sys);
+    for (int b = 0; b < sys->n_sys; b++) {
+        base[b] = sys->hst[b].res_f;
+        if (sys->hst[b].status == FFMIN_ERR_NONFINITE) res = FFMIN_ERR_NONFINITE;
+    }
+    if ((st = eval_slot(sys, V_XIN, EV_E, V_R, h, 1)) != FFMIN_OK) return st;
+    for (int b = 0; b < sys->n_sys; b++) {
+        de_host[b] = sys->hst[b].res_f - base[b];
+        if (sys->hst[b].status == FFMIN_ERR_NONFINITE) res = FFMIN_ERR_NONFINITE;
+    }
+    st = leave(sys);
+    return st != FFMIN_OK ? st : res;
+}
+
 static ffmin_status check_options(ffmin_system *sys, const ffmin_options *o) {
     if (!o) return fail(sys, FFMIN_ERR_INVALID_ARG, "options is NULL");
     if (o->method < FFMIN_GD || o->method > FFMIN_OGM) return fail(sys, FFMIN_ERR_INVALID_ARG, "bad method");
@@ -767,6 +798,8 @@ static ffmin_status check_options(ffmin_system *sys, const ffmin_options *o) {
         return fail(sys, FFMIN_ERR_INVALID_ARG, "GRADFREE needs one system and delta > 0");
     if (o->use_learned_precond && !sys->have_precond)
         return fail(sys, FFMIN_ERR_INVALID_ARG, "no preconditioner weights set");
+    if (o->fgm_restart != 0 && o->fgm_restart != 1)
+        return fail(sys, FFMIN_ERR_INVALID_ARG, "fgm_restart must be 0 or 1");
     if (o->record_dev && (o->record_every < 1 || o->record_slots < 1))
         return fail(sys, FFMIN_ERR_INVALID_ARG, "recording needs record_every >= 1 and record_slots >= 1");
     return FFMIN_OK;
@@ -805,6 +838,7 @@ static ffmin_status minimize_dev(ffmin_system *sys, double *x_dev, const ffmin_o
         S.kplus = o->k_plus;
         S.kminus = o->k_minus;
         S.eps_h = o->eps_h;
+        S.fgm_restart = o->fgm_restart;
         S.precond_on = (o->use_learned_precond && o->method == FFMIN_LBFGS) ? 1 : 0;
         S.rec_ptr = o->record_dev;
         S.rec_every = o->record_dev ? o->record_every : 0;
@@ -840,6 +874,14 @@ static ffmin_status minimize_dev(ffmin_system *sys, double *x_dev, const ffmin_o
     }
     sys->last_ticks = ticks;
     sys->last_launches = ticks * kernels_per_tick(sys);
+    if (timeout) {
+        // a step accepted in the last round is written into X (FGM: the best
+        // point) by the next round's update kernel: run that update once more
+        // so that the returned point is the one the counters describe
+        CK(launch_update(c, sys->stream));
+        if (c.sep_reduce) CK(launch_sysreduce(c, 0, sys->stream));
+        sys->last_launches += 1 + (c.sep_reduce ? 1 : 0);
+    }
     st = download_states(sys);
     if (st != FFMIN_OK) return st;
     const int slot = o->method == FFMIN_FGM ? V_XB : V_X;
@@ -855,6 +897,11 @@ static ffmin_status minimize_dev(ffmin_system *sys, double *x_dev, const ffmin_o
         r.grad_evals = S.neg;
         r.ls_failures = S.lsf;
         r.stop_reason = (timeout && S.active) ? FFMIN_ERR_TIMEOUT : S.status;
+        if (timeout && S.active) {  // still running: the last accepted (FGM: best) point
+            const bool fgm = S.method == FFMIN_FGM;
+            r.energy = fgm ? S.fb : S.f;
+            r.grad_inf = fgm ? (S.xb_known ? S.xb_ginf : std::nan("")) : S.ginf;
+        }
         const int64_t nb = S.natoms;
         pairs += (int64_t)(S.ne + S.neg) * nb * (nb - 1) / 2;
     }

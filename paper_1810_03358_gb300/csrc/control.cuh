@@ -11,9 +11,9 @@
 // The machine restates, step for step, Algorithms 1-6 of arXiv 1810.03358
 // (Sections 5.1-5.2) and the adaptive gradient descent of Section 3 (Eq. 4),
 // with these readings where the paper is silent: normalised directions,
-// warm-started steps, one restart after a failed line search, the
-// function-value momentum restart of FGM, skipped L-BFGS pairs with
-// <s, y> <= 0.  The L-BFGS two-loop recursion (Algorithm 3) is evaluated from
+// warm-started steps, one restart after a failed line search, skipped
+// L-BFGS pairs with <s, y> <= 0; FGM's function-value momentum restart is
+// an option (Algorithm 1 itself has none).  The L-BFGS two-loop recursion (Algorithm 3) is evaluated from
 // maintained inner products <s_a, y_b> and <s_a, g> (same alpha and beta as
 // the vector recursion) so that it costs two vector passes instead of 2m.
 #pragma once
@@ -350,7 +350,9 @@ __device__ void fgm_next_w(SysState &S) {
 
 __device__ void fgm_accept(SysState &S, double h, double fnew) {
     const double th = fgm_theta(S.th_prev);
-    const int restart = fnew > S.fx;
+    // Algorithm 1 keeps its momentum (and the best point); the optional
+    // function-value restart drops it when the new iterate is worse
+    const int restart = S.fgm_restart && fnew > S.fx;
     const int best = fnew < S.fb;
     S.upd.op = U_FGM_ACCEPT;
     S.upd.h = h;

@@ -109,6 +109,7 @@ struct SysState {
     double th_prev, fx, fb, fw, xb_ginf;
     double ogm_t;  // OGM: t_k
     int32_t xb_known, result_slot;
+    int32_t fgm_restart, fgm_pad;  // 1: function-value momentum restart (not in Algorithm 1)
     // result
     double res_f, res_ginf;
     // learned preconditioner in use for this run

@@ -13,10 +13,12 @@
 // i < j pairs of one system, Coulomb + Lennard-Jones, no bonded terms:
 // rows of 128 i-atoms against 8 j-chunks, partial rows to the scratch, then
 // one thread per atom sums its chunks in a fixed order and the last block
-// sums the block energies.
+// sums the block energies and flags a non-finite energy or gradient (two
+// coincident atoms), which the call reports after synchronising its stream.
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <mutex>
 
 #include "ffmin.h"
 
@@ -27,13 +29,18 @@ constexpr int NA_TJ = 128;      // j atoms staged per shared-memory tile
 constexpr int NA_CHUNKS = 8;    // j chunks per row
 constexpr int NA_MAX_ATOMS = 8192;
 constexpr int NA_MAX_BLOCKS = (NA_MAX_ATOMS + NA_TI - 1) / NA_TI;
-// doubles: partial rows [chunk][atom][4], block energies, one 8-byte ticket
+// doubles: partial rows [chunk][atom][4], block energies, one 8-byte word
+// holding the last-block ticket and the non-finite flag (two uint32)
 constexpr size_t NA_SCRATCH = (size_t)NA_CHUNKS * NA_MAX_ATOMS * 4 + NA_MAX_BLOCKS + 1;
 
 __device__ __align__(256) double g_noalloc_scratch[NA_SCRATCH];
 
 constexpr int NA_MAX_DEVICES = 64;
-double *g_scratch_ptr[NA_MAX_DEVICES];  // device address of the array, per device
+// device address of the array per device ordinal, looked up once in the
+// device's primary context (a cudaDeviceReset or another context would need
+// a new lookup); the lock guards the first lookup against concurrent callers
+double *g_scratch_ptr[NA_MAX_DEVICES];
+std::mutex g_scratch_lock;
 
 struct NaArgs {
     const double *x, *q, *sigma, *eps;
@@ -42,7 +49,7 @@ struct NaArgs {
     double *g, *e;
     double *part;      // [NA_CHUNKS][NA_MAX_ATOMS][4]
     double *eblock;    // [NA_MAX_BLOCKS]
-    unsigned int *ticket;
+    unsigned int *ticket;  // [0] last-block ticket, [1] non-finite flag
 };
 
 __device__ __forceinline__ void na_atom(const NaArgs &a, int j, double4_32a &p, double2 &c) {
@@ -104,6 +111,7 @@ __global__ void __launch_bounds__(NA_TI) k_na_final(NaArgs a) {
     __shared__ double se[NA_TI];
     const int i = blockIdx.x * NA_TI + threadIdx.x;
     double e = 0.0;
+    bool bad = false;
     if (i < a.n) {
         double g0 = 0.0, g1 = 0.0, g2 = 0.0;
         for (int ch = 0; ch < NA_CHUNKS; ch++) {
@@ -112,9 +120,10 @@ __global__ void __launch_bounds__(NA_TI) k_na_final(NaArgs a) {
         }
         a.g[3 * i] = g0; a.g[3 * i + 1] = g1; a.g[3 * i + 2] = g2;
         e *= 0.5;  // each pair appears in two rows
+        bad = !isfinite(g0) || !isfinite(g1) || !isfinite(g2);
     }
     se[threadIdx.x] = e;
-    __syncthreads();
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(a.ticket + 1, 1u);
     if (threadIdx.x == 0) {
         double s = 0.0;
         for (int t = 0; t < NA_TI; t++) s += se[t];
@@ -126,6 +135,7 @@ __global__ void __launch_bounds__(NA_TI) k_na_final(NaArgs a) {
             double tot = 0.0;
             for (int b = 0; b < (int)gridDim.x; b++) tot += __ldcg(&a.eblock[b]);
             *a.e = tot;
+            if (!isfinite(tot)) atomicOr(a.ticket + 1, 1u);
             *a.ticket = 0u;
         }
     }
@@ -140,29 +150,40 @@ extern "C" ffmin_status ffmin_pair_energy_grad_noalloc(const double *x_dev, cons
     if (n_atoms < 1 || n_atoms > NA_MAX_ATOMS || !x_dev || !charge_dev || !sigma_dev || !epsilon_dev ||
         !g_dev || !e_dev)
         return FFMIN_ERR_INVALID_ARG;  // sizes beyond the fixed scratch are refused
+    if (!(coulomb_c >= 0.0) || !std::isfinite(coulomb_c)) return FFMIN_ERR_INVALID_ARG;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) return FFMIN_ERR_CUDA;
-    if (!g_scratch_ptr[dev]) {  // first call on this device: look up the array's device address
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return FFMIN_ERR_CUDA;
-        g_scratch_ptr[dev] = (double *)p;
+    double *scr;
+    {
+        std::lock_guard<std::mutex> lock(g_scratch_lock);
+        if (!g_scratch_ptr[dev]) {  // first call on this device: look up the array's device address
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return FFMIN_ERR_CUDA;
+            g_scratch_ptr[dev] = (double *)p;
+        }
+        scr = g_scratch_ptr[dev];
     }
-    double *scr = g_scratch_ptr[dev];
     cudaStream_t s = (cudaStream_t)cuda_stream;
     NaArgs a;
     a.x = x_dev; a.q = charge_dev; a.sigma = sigma_dev; a.eps = epsilon_dev;
     a.n = n_atoms;
-    a.sqrt_c = std::sqrt(coulomb_c > 0.0 ? coulomb_c : 1389.38757 / 4.184);
+    a.sqrt_c = std::sqrt(coulomb_c == 0.0 ? 1389.38757 / 4.184 : coulomb_c);
     a.g = g_dev;
     a.e = e_dev;
     a.part = scr;
     a.eblock = scr + (size_t)NA_CHUNKS * NA_MAX_ATOMS * 4;
     a.ticket = (unsigned int *)(a.eblock + NA_MAX_BLOCKS);
-    // the ticket must start at zero on every call (the array keeps the last
-    // call's contents)
+    // the ticket and the flag must start at zero on every call (the array
+    // keeps the last call's contents)
     if (cudaMemsetAsync(a.ticket, 0, sizeof(double), s) != cudaSuccess) return FFMIN_ERR_CUDA;
     const int blocks = (n_atoms + NA_TI - 1) / NA_TI;
     k_na_rows<<<dim3(blocks, NA_CHUNKS), NA_TI, 0, s>>>(a);
     k_na_final<<<blocks, NA_TI, 0, s>>>(a);
-    return cudaGetLastError() == cudaSuccess ? FFMIN_OK : FFMIN_ERR_CUDA;
+    if (cudaGetLastError() != cudaSuccess) return FFMIN_ERR_CUDA;
+    // the status needs the flag: read it back (pageable host word) and wait
+    unsigned int flag = 0u;
+    if (cudaMemcpyAsync(&flag, a.ticket + 1, sizeof(flag), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return FFMIN_ERR_CUDA;
+    return flag ? FFMIN_ERR_NONFINITE : FFMIN_OK;
 }

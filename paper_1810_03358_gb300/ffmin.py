@@ -49,7 +49,8 @@ class ffmin_options(C.Structure):
                 ("gradfree_delta", C.c_double), ("seed", C.c_uint64), ("gradfree_parts", C.c_int32),
                 ("gradfree_margin", C.c_double),
                 ("use_learned_precond", C.c_int32), ("max_ticks", C.c_int32),
-                ("record_dev", C.c_void_p), ("record_every", C.c_int32), ("record_slots", C.c_int32)]
+                ("record_dev", C.c_void_p), ("record_every", C.c_int32), ("record_slots", C.c_int32),
+                ("fgm_restart", C.c_int32)]
 
 
 class ffmin_result(C.Structure):
@@ -60,7 +61,7 @@ class ffmin_result(C.Structure):
 
 EXPORTS = ["ffmin_options_default", "ffmin_status_string", "ffmin_create", "ffmin_destroy",
            "ffmin_n_atoms", "ffmin_atom_offset", "ffmin_energy", "ffmin_energy_grad",
-           "ffmin_energy_grad_host", "ffmin_minimize", "ffmin_minimize_host",
+           "ffmin_energy_grad_host", "ffmin_energy_delta", "ffmin_minimize", "ffmin_minimize_host",
            "ffmin_set_precond", "ffmin_time_pair_kernel", "ffmin_last_stats",
            "ffmin_last_error", "ffmin_pair_energy_grad_noalloc", "ffmin_neighbour_counts",
            "ffmin_mlp_train", "ffmin_mlp_work_floats", "ffmin_autotune", "ffmin_alu_peak",
@@ -94,6 +95,7 @@ def lib():
     L.ffmin_energy.argtypes = [vp, vp, _dp]
     L.ffmin_energy_grad.argtypes = [vp, vp, _dp, vp]
     L.ffmin_energy_grad_host.argtypes = [vp, _dp, _dp, _dp]
+    L.ffmin_energy_delta.argtypes = [vp, vp, vp, C.c_double, _dp]
     L.ffmin_minimize.argtypes = [vp, vp, C.POINTER(ffmin_options), C.POINTER(ffmin_result)]
     L.ffmin_minimize_host.argtypes = [vp, _dp, C.POINTER(ffmin_options), C.POINTER(ffmin_result)]
     L.ffmin_set_precond.argtypes = [vp, C.POINTER(C.c_uint16), C.c_int32]
@@ -234,6 +236,16 @@ def ffmin_energy_grad_host(handle, x_host, g_host=None, n_sys=1):
     return e
 
 
+def ffmin_energy_delta(handle, x, r, h, n_sys=1):
+    """E(x + h r) - E(x) per system, as a line-search trial evaluates it."""
+    de = np.zeros(n_sys)
+    n = ffmin_n_atoms(handle)
+    st = lib().ffmin_energy_delta(C.c_void_p(handle), _dev_ptr(x, n), _dev_ptr(r, n), float(h),
+                                  de.ctypes.data_as(_dp))
+    _check(st, handle)
+    return de
+
+
 def _results(rs):
     out = []
     for r in rs:
@@ -334,6 +346,9 @@ class System:
         e = ffmin_energy_grad(self.handle, x, g, self.n_sys)
         return e, g
 
+    def energy_delta(self, x, r, h):
+        return ffmin_energy_delta(self.handle, x, r, h, self.n_sys)
+
     def minimize(self, x, **opts):
         o = ffmin_options_default(**opts)
         return ffmin_minimize(self.handle, x, o, self.n_sys)
@@ -366,11 +381,22 @@ def ffmin_pair_energy_grad_noalloc(x, charge, sigma, epsilon, g, e, coulomb_c=0.
     no allocation inside the library (torch FP64 CUDA tensors: x [3N],
     charge / sigma / epsilon [N], g [3N] out, e [1] out).  Returns the status;
     raises FfminError on failure."""
+    import torch
     n = int(charge.numel())
-    st = lib().ffmin_pair_energy_grad_noalloc(
-        C.c_void_p(x.data_ptr()), C.c_void_p(charge.data_ptr()), C.c_void_p(sigma.data_ptr()),
-        C.c_void_p(epsilon.data_ptr()), n, float(coulomb_c), C.c_void_p(g.data_ptr()),
-        C.c_void_p(e.data_ptr()), C.c_void_p(_stream_handle(stream)))
+
+    def per_atom(t, what, count):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+            raise FfminError(FFMIN_ERR_INVALID_ARG, f"{what}: expected a contiguous float64 CUDA tensor")
+        if t.numel() != count:
+            raise FfminError(FFMIN_ERR_INVALID_ARG, f"{what}: expected {count} values, got {t.numel()}")
+        return C.c_void_p(t.data_ptr())
+
+    px, pg = per_atom(x, "x", 3 * n), per_atom(g, "g", 3 * n)
+    pq, ps, pe = per_atom(charge, "charge", n), per_atom(sigma, "sigma", n), per_atom(epsilon, "epsilon", n)
+    if not (isinstance(e, torch.Tensor) and e.is_cuda and e.dtype == torch.float64 and e.numel() >= 1):
+        raise FfminError(FFMIN_ERR_INVALID_ARG, "e: expected a float64 CUDA tensor with at least one value")
+    st = lib().ffmin_pair_energy_grad_noalloc(px, pq, ps, pe, n, float(coulomb_c), pg,
+                                              C.c_void_p(e.data_ptr()), C.c_void_p(_stream_handle(stream)))
     if st != FFMIN_OK:
         raise FfminError(st, "ffmin_pair_energy_grad_noalloc failed")
     return st

@@ -27,3 +27,47 @@ def split(arr, systems):
         out.append(np.asarray(arr[k:k + n]).reshape(-1, 3))
         k += n
     return out
+
+
+# ---- oracle runs in worker processes (spawned, never forked after CUDA) ----
+def _oracle_energy_terms(s, x):
+    from oracle import oracle
+    d, st, g = oracle.energy_terms(s, x, grad=True)
+    return d, st, g
+
+
+def _oracle_minimize(s, x, kw):
+    from oracle import oracle
+    return oracle.minimize(s, x, **kw)
+
+
+def oracle_pool(workers=None):
+    """A process pool for independent oracle calls (one per system of a
+    batch), started with 'spawn' so that no worker inherits a CUDA context."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import os
+    n = workers or max(1, min(16, os.cpu_count() or 1))
+    return cf.ProcessPoolExecutor(max_workers=n, mp_context=mp.get_context("spawn"))
+
+
+def oracle_map(fn, *iterables):
+    """fn over the arguments in worker processes; results in order."""
+    with oracle_pool() as pool:
+        return list(pool.map(fn, *iterables))
+
+
+def _oracle_delta_rows(s, x, xp, i0, i1):
+    from oracle import oracle
+    return oracle.energy_delta(s, x, xp, rows=(i0, i1))
+
+
+def oracle_energy_delta(s, x, xp, blocks=64):
+    """The oracle's term-by-term E(xp) - E(x) and sum |term differences|, its
+    pair rows split into blocks of about equal pair counts over the pool."""
+    n = s.n_atoms
+    cuts = sorted({int(round(n * (1.0 - np.sqrt(1.0 - k / blocks)))) for k in range(blocks + 1)})
+    lo, hi = cuts[:-1], cuts[1:]
+    parts = oracle_map(_oracle_delta_rows, [s] * len(lo), [x] * len(lo), [xp] * len(lo), lo, hi)
+    assert all(p[2] == 0 for p in parts)
+    return sum(p[0] for p in parts), sum(p[1] for p in parts)

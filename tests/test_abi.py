@@ -88,6 +88,7 @@ def test_option_defaults_agree_with_the_oracle(built, oracle_mod):
     g = ffmin.ffmin_options_default()
     o, _ = oracle_mod.options()
     for k in ("method", "cg_variant", "ls", "lbfgs_m", "gtol_inf", "max_iter", "max_evals", "h0", "k_plus",
-              "k_minus", "eps_h", "ls_par_K", "ls_par_g0", "gradfree_delta", "gradfree_parts"):
+              "k_minus", "eps_h", "ls_par_K", "ls_par_g0", "gradfree_delta", "gradfree_parts", "fgm_restart"):
         assert getattr(g, k) == getattr(o, k), k
     assert (g.h0, g.k_plus, g.k_minus, g.ls_par_K, g.lbfgs_m, g.gtol_inf) == (0.1, 2.0, 0.5, 2, 10, 0.1)
+    assert g.fgm_restart == 0  # Algorithm 1 as printed

@@ -71,8 +71,8 @@ def oracle_sensitivity(oracle_mod, s, xo, ro, kw, members=3, eps=1e-15):
     return de, dx, same
 
 
-def prefix_parity(oracle_mod, s, xg, rg, kw):
-    xo, ro = oracle_mod.minimize(s, s.x, **kw)
+def prefix_parity(oracle_mod, s, xg, rg, kw, ref=None):
+    xo, ro = ref if ref is not None else oracle_mod.minimize(s, s.x, **kw)
     assert rg["status_name"] == STATUS[ro["status_name"]], (rg, ro)
     for k in ("iterations", "energy_evals", "grad_evals", "ls_failures"):
         assert rg[k] == ro[k], (k, rg, ro)
@@ -130,6 +130,35 @@ def test_prefix_methods(ff, oracle_mod, method, n, seed):
     kw = dict(method=method, max_iter=PREFIX)
     xg, rg, _ = run_gpu(ff, [s], 0, **kw)
     prefix_parity(oracle_mod, s, xg[0], rg[0], kw)
+
+
+@pytest.mark.parametrize("ls", [0, 2])
+@pytest.mark.parametrize("n,seed", [(40, 21), (130, 22)])
+def test_prefix_fgm_restart_option(ff, oracle_mod, n, seed, ls):
+    # FGM with the optional function-value momentum restart (Algorithm 1
+    # itself, the default, is covered by test_prefix_methods)
+    s = synth.make_system(n, seed)
+    kw = dict(method=1, ls=ls, max_iter=PREFIX, fgm_restart=1)
+    xg, rg, _ = run_gpu(ff, [s], 0, **kw)
+    prefix_parity(oracle_mod, s, xg[0], rg[0], kw)
+
+
+def test_fgm_literal_long_run_returns_best_point(ff, oracle_mod):
+    # Algorithm 1 as printed is non-monotone and, from these clashing starts,
+    # does not converge (beta -> 1, steps of tens of A); beyond the prefix the
+    # GPU and oracle trajectories separate, but the GPU must return its best
+    # point with that point's energy, at least as good as the oracle's best
+    # point over the first 60 steps (where both take the same steps)
+    s = synth.make_system(40, 21)
+    kw = dict(method=1, max_iter=400)
+    xg, rg, _ = run_gpu(ff, [s], 0, **kw)
+    r = rg[0]
+    assert r["status_name"] == "max_iter" and r["iterations"] == 400, r
+    e1, g1 = oracle_mod.energy_grad(s, xg[0])
+    assert abs(e1 - r["energy"]) <= 1e-9 * abs(e1)
+    assert abs(np.abs(g1).max() - r["grad_inf"]) <= 1e-9 * np.abs(g1).max()
+    xo, ro = oracle_mod.minimize(s, s.x, **dict(kw, max_iter=PREFIX))
+    assert r["energy"] <= ro["energy"] * (1 + 1e-8)
 
 
 @pytest.mark.parametrize("variant", range(7))
@@ -208,6 +237,30 @@ def test_evaluation_cap(ff, oracle_mod):
     prefix_parity(oracle_mod, s, xg[0], rg[0], kw)
 
 
+@pytest.mark.parametrize("method", [3, 1, 2])
+def test_round_limit_timeout(ff, oracle_mod, method):
+    # the host-side bound on device rounds (options.max_ticks, a safety net
+    # that needs no device-side wait): the run stops with FFMIN_ERR_TIMEOUT
+    # after 16 rounds (two graph replays), returning its last accepted point
+    # (FGM: its best point) with that point's energy, which is the oracle's
+    # point after the same number of accepted steps
+    s = synth.make_system(80, 26)
+    xg, rg, st = run_gpu(ff, [s], 0, method=method, max_ticks=16)
+    r = rg[0]
+    assert r["status_name"] == "timeout", r
+    assert st["ticks"] == 16
+    k = r["iterations"]
+    assert k >= 1
+    xo, ro = oracle_mod.minimize(s, s.x, method=method, max_iter=k)
+    assert np.abs(xg[0] - xo).max() <= 1e-6
+    e1, g1 = oracle_mod.energy_grad(s, xg[0])
+    assert abs(r["energy"] - e1) <= 1e-9 * abs(e1)
+    if np.isfinite(r["grad_inf"]):
+        assert abs(r["grad_inf"] - np.abs(g1).max()) <= 1e-9 * np.abs(g1).max()
+    else:
+        assert method == 1
+
+
 def test_already_converged_start(ff, oracle_mod):
     s = synth.make_system(25, 30)
     xo, ro = oracle_mod.minimize(s, s.x, method=3)
@@ -219,8 +272,10 @@ def test_already_converged_start(ff, oracle_mod):
 
 @pytest.mark.parametrize("method", [0, 1, 2, 3])
 def test_full_runs_ensemble(ff, oracle_mod, method):
+    # FGM with its optional restart: Algorithm 1 as printed does not converge
+    # from this start (oracle and GPU alike)
     s = synth.make_system(40, 21)
-    kw = dict(method=method, max_iter=100000)
+    kw = dict(method=method, max_iter=100000, fgm_restart=int(method == 1))
     xg, rg, _ = run_gpu(ff, [s], 0, **kw)
     ensemble_parity(oracle_mod, s, xg[0], rg[0], kw)
 
@@ -261,7 +316,7 @@ def test_mixed_fp32_then_fp64(ff, oracle_mod, method):
     # FP64 phase re-evaluates and finishes; the returned point is certified
     # by the oracle's own gradient, and its energy is reported in FP64
     s = synth.make_system(120, 27)
-    kw = dict(method=method, max_iter=100000)
+    kw = dict(method=method, max_iter=100000, fgm_restart=int(method == 1))
     xg, rg, _ = run_gpu(ff, [s], 1, **kw)
     r = rg[0]
     assert r["status_name"] == "ok", r

@@ -226,3 +226,33 @@ def test_atom_gradient_equals_full_gradient_row(oracle_mod):
     e, g = oracle_mod.energy_grad(s, s.x)
     for i in (0, 1, 12, 23, 24):
         assert np.allclose(oracle_mod.atom_gradient(s, s.x, i), g[i], rtol=1e-12, atol=1e-9)
+
+
+@pytest.mark.parametrize("excl", [0, 1])
+def test_energy_delta_definition(oracle_mod, excl):
+    # the term-by-term difference equals the difference of the two totals
+    # (rounding of the totals: ~u sum|terms|), vanishes at xp = x, splits
+    # over row blocks, and its slope at h -> 0 is the directional derivative
+    # <grad E, r> of the (separately pinned) gradient
+    s = synth.make_system(60, 41)
+    s.exclusions, s.scale14 = excl, 0.5
+    rng = np.random.default_rng(3)
+    r = rng.normal(size=s.x.shape)
+    r /= np.linalg.norm(r)
+    d0, a0, st = oracle_mod.energy_delta(s, s.x, s.x)
+    assert st == 0 and d0 == 0.0 and a0 == 0.0
+    tot = oracle_mod.energy_terms(s, s.x)[0]
+    for h in (1e-3, 0.05, 0.5):
+        xp = s.x + h * r
+        d, a, st = oracle_mod.energy_delta(s, s.x, xp)
+        assert st == 0 and a >= abs(d)
+        ref = oracle_mod.energy(s, xp) - oracle_mod.energy(s, s.x)
+        assert abs(d - ref) <= 1e-14 * tot["sum_abs"]
+        parts = [oracle_mod.energy_delta(s, s.x, xp, rows=(i0, i0 + 17))[0] for i0 in range(0, 60, 17)]
+        assert sum(parts) == pytest.approx(d, rel=1e-12, abs=1e-12 * a)
+    e, g = oracle_mod.energy_grad(s, s.x)
+    slope = float(np.sum(g * r))
+    h = 1e-6
+    dp = oracle_mod.energy_delta(s, s.x, s.x + h * r)[0]
+    dm = oracle_mod.energy_delta(s, s.x, s.x - h * r)[0]
+    assert (dp - dm) / (2 * h) == pytest.approx(slope, rel=1e-5)

@@ -189,20 +189,105 @@ def test_lbfgs_two_loop_equals_bfgs_matrix(oracle_mod, count, diag):
 
 def test_fgm_theta_recurrence(oracle_mod):
     # theta_k solves theta^2 = (1 - theta) theta_{k-1}^2 (Alg. 1's update is the
-    # positive root), theta_{-1} = 1; beta_k in [0, 1)
+    # positive root), theta_{-1} = 1; the literal method never resets theta;
+    # beta_k in [0, 1)
     A, b, _ = spd(10, 100.0, 4)
     xo, r = oracle_mod.minimize_fn(quad_fg(A, b), np.zeros(10), method=oracle_mod.FGM,
                                    gtol_inf=1e-6, max_iter=500)
     tr = oracle_mod.trace()
     th = np.concatenate([[1.0], tr["theta"]])
     assert len(th) > 5
-    # only uninterrupted stretches (a restart resets theta to 1)
-    for k in range(1, len(th)):
-        if th[k] < th[k - 1]:
-            assert th[k] ** 2 == pytest.approx((1 - th[k]) * th[k - 1] ** 2, rel=1e-12)
+    assert np.all(np.diff(th) < 0.0)
+    assert np.allclose(th[1:] ** 2, (1 - th[1:]) * th[:-1] ** 2, rtol=1e-12, atol=0.0)
     assert np.all(tr["beta"] >= 0.0) and np.all(tr["beta"] < 1.0)
-    assert r["status_name"] == "ok"
-    assert np.abs(xo - np.linalg.solve(A, b)).max() < 1e-4
+    # with LS_H the literal method need not converge here; it returns its best point
+    assert r["energy"] == pytest.approx(min(0.0, tr["f"].min()), rel=1e-12)
+    assert 0.5 * xo @ A @ xo - b @ xo == pytest.approx(r["energy"], rel=1e-12)
+
+
+def fista_form(A, b, L, x0, steps):
+    """Nesterov's accelerated gradient in the t-form of Beck and Teboulle
+    (SIAM J. Imaging Sci. 2009, FISTA with an identity proximal map):
+    t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2, y = x_k + (t_{k-1} - 1)/t_k (x_k - x_{k-1}),
+    x_{k+1} = y - grad f(y) / L.  Started from t = 1 then t = (1 + sqrt 5)/2,
+    the start of Nesterov's constant-step scheme (2.2.19) with
+    alpha_0 = (sqrt 5 - 1)/2 = 1/t.  Returns the iterates x_1 .. x_steps."""
+    x, xp = x0.copy(), x0.copy()
+    t_prev, t = 1.0, 0.5 * (1.0 + np.sqrt(5.0))
+    out = []
+    for _ in range(steps):
+        y = x + (t_prev - 1.0) / t * (x - xp)
+        xp, x = x, y - (A @ y - b) / L
+        t_prev, t = t, 0.5 * (1.0 + np.sqrt(1.0 + 4.0 * t * t))
+        out.append(x.copy())
+    return out
+
+
+@pytest.mark.parametrize("N", [1, 2, 7, 40])
+def test_fgm_fixed_step_equals_fista_form(oracle_mod, N):
+    # Algorithm 1 with the fixed step 1/L in place of the line search is
+    # Nesterov's method; its theta / beta recurrence (beta_k and the
+    # extrapolation w^k = x^k + beta_k (x^k - x^{k-1})) must give the same
+    # iterates as the independent t-form above.  A dropped term of beta, a
+    # theta_k written for theta_{k-1} or a sign slip in w breaks this.
+    A, b, lam = spd(12, 200.0, 5)
+    L = lam[-1]
+    x0 = np.random.default_rng(2).normal(size=12)
+    xs = fista_form(A, b, L, x0, N)
+    fs = np.array([0.5 * x @ A @ x - b @ x for x in xs])
+    xo, r = oracle_mod.minimize_fn(quad_fg(A, b), x0, method=oracle_mod.FGM, gtol_inf=1e-14,
+                                   max_iter=N, fgm_step=1.0 / L)
+    assert r["iterations"] == N
+    tr = oracle_mod.trace()
+    assert np.allclose(tr["f"], fs, rtol=1e-12, atol=1e-12)
+    # the method returns its best point x_* (Algorithm 1)
+    f0 = 0.5 * x0 @ A @ x0 - b @ x0
+    best = x0 if f0 <= fs.min() else xs[int(np.argmin(fs))]
+    assert np.abs(xo - best).max() <= 1e-11 * (1.0 + np.abs(best).max())
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_fgm_rate_on_convex_quadratics(oracle_mod, seed):
+    # Nesterov (Introductory Lectures 2004, Theorem 2.2.3) for scheme (2.2.19)
+    # with mu = 0 and alpha_0 = (sqrt 5 - 1)/2, i.e. gamma_0 = L:
+    #   f(x_k) - f* <= 4 (f(x_0) - f* + L R^2 / 2) / (k + 2)^2
+    n = 30
+    A, b, lam = spd(n, 1000.0, seed)
+    L = lam[-1]
+    xs = np.linalg.solve(A, b)
+    fstar = 0.5 * xs @ A @ xs - b @ xs
+    x0 = np.zeros(n)
+    oracle_mod.minimize_fn(quad_fg(A, b), x0, method=oracle_mod.FGM, gtol_inf=1e-9,
+                           max_iter=2000, fgm_step=1.0 / L)
+    f = oracle_mod.trace()["f"] - fstar
+    k = np.arange(1, len(f) + 1)
+    f0 = 0.5 * x0 @ A @ x0 - b @ x0 - fstar
+    assert len(f) > 500
+    assert np.all(f <= 4.0 * (f0 + 0.5 * L * np.sum((x0 - xs) ** 2)) / (k + 2) ** 2 * (1 + 1e-9))
+
+
+def test_fgm_literal_keeps_best_point_and_restart_option(oracle_mod):
+    # Section 5.1: FGM is non-monotone (f(x^{k+1}) > f(x^k) happens) and
+    # returns the best point x_*.  On the clashing force-field start the
+    # literal method reaches its best point early and then wanders with
+    # beta -> 1; the optional function-value restart (not in Algorithm 1)
+    # resets theta and converges.
+    s = synth.make_system(40, 21)
+    e0 = oracle_mod.energy(s, s.x)
+    xo, r = oracle_mod.minimize(s, s.x, method=oracle_mod.FGM, max_iter=400)
+    tr = oracle_mod.trace()
+    assert r["status_name"] == "max_iter" and len(tr["f"]) == 400
+    assert np.any(np.diff(tr["f"]) > 0.0)  # non-monotone
+    assert np.all(np.diff(np.concatenate([[1.0], tr["theta"]])) < 0.0)  # never reset
+    best = min(e0, tr["f"].min())
+    e1, g1 = oracle_mod.energy_grad(s, xo)
+    assert r["energy"] == pytest.approx(best, rel=1e-12)
+    assert e1 == pytest.approx(best, rel=1e-12)
+    assert np.abs(g1).max() == pytest.approx(r["grad_inf"], rel=1e-12)
+    xo, r = oracle_mod.minimize(s, s.x, method=oracle_mod.FGM, max_iter=20000, fgm_restart=1)
+    th = oracle_mod.trace()["theta"]
+    assert np.any(np.diff(th) > 0.0)  # restarts happened
+    assert r["status_name"] == "ok" and r["energy"] < best
 
 
 def test_ogm_first_step_is_cauchy_step(oracle_mod):
@@ -267,9 +352,12 @@ def test_ogm_rate_on_convex_quadratics(oracle_mod, seed):
 
 @pytest.mark.parametrize("method", ["GD", "FGM", "CG", "LBFGS"])
 def test_force_field_minimizers_converge(oracle_mod, method):
+    # (FGM with the optional momentum restart: the literal Algorithm 1 does
+    # not converge from this start, see the test above)
     s = synth.make_system(40, 21)
     e0 = oracle_mod.energy(s, s.x)
-    xo, r = oracle_mod.minimize(s, s.x, method=getattr(oracle_mod, method), max_iter=20000)
+    xo, r = oracle_mod.minimize(s, s.x, method=getattr(oracle_mod, method), max_iter=20000,
+                                fgm_restart=int(method == "FGM"))
     assert r["status_name"] == "ok", r
     assert r["grad_inf"] < 0.1
     e1, g1 = oracle_mod.energy_grad(s, xo)
