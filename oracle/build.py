@@ -22,7 +22,7 @@ def build(force: bool = False) -> str:
         if os.path.getmtime(LIB) >= newest:
             return LIB
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off",
+    cmd = ["gcc", "-O3", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off",
            "-Wall", "-Wextra", "-Wdouble-promotion", "-o", tmp] + srcs + ["-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB)

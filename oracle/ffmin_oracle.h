@@ -58,6 +58,13 @@ enum { ORC_OK = 0, ORC_NONFINITE = 1, ORC_LINESEARCH = 2, ORC_MAX_ITER = 3, ORC_
  * not finite. */
 int orc_energy_terms(const orc_ff *ff, const double *x, double *grad, orc_terms *out);
 
+/* orc_energy_terms restricted to the pairs (i, j), i < j, with i in [i0, i1)
+ * (plus the bonded terms when i0 == 0); the gradient of these terms is ADDED
+ * into grad [3N] (may be NULL).  The blocks of a partition of [0, N) sum to
+ * the whole energy and gradient: independent workers may split the rows. */
+int orc_energy_rows(const orc_ff *ff, const double *x, int32_t i0, int32_t i1, double *grad,
+                    orc_terms *out);
+
 /* E(xp) - E(x) summed term by term (each term at xp minus itself at x),
  * *sum_abs = sum over terms of |difference|: the definition of a line-search
  * trial's energy change.  Pairs (i, j), i < j, with i in [i0, i1); the

@@ -206,6 +206,53 @@ static double dihedral_term(const double *xi, const double *xj, const double *xk
     return e;
 }
 
+/* The bonded terms (stretch, bend, torsion of Section 2) added into *t and,
+ * when grad != NULL, their gradient into grad. */
+static void add_bonded(const orc_ff *ff, const double *x, double *grad, orc_terms *tp) {
+    orc_terms t = *tp;
+    /* bonds */
+    for (int b = 0; b < ff->n_bonds; b++) {
+        int i = ff->bond_idx[2 * b], j = ff->bond_idx[2 * b + 1];
+        double gi[3] = {0.0}, gj[3] = {0.0};
+        double e = bond_term(x + 3 * i, x + 3 * j, ff->bond_k[b], ff->bond_r0[b],
+                             grad ? gi : NULL, gj);
+        t.stretch += e;
+        t.sum_abs += fabs(e);
+        if (grad)
+            for (int a = 0; a < 3; a++) { grad[3 * i + a] += gi[a]; grad[3 * j + a] += gj[a]; }
+    }
+    /* angles */
+    for (int b = 0; b < ff->n_angles; b++) {
+        int i = ff->angle_idx[3 * b], j = ff->angle_idx[3 * b + 1], k = ff->angle_idx[3 * b + 2];
+        double gi[3] = {0.0}, gj[3] = {0.0}, gk[3] = {0.0};
+        double e = angle_term(x + 3 * i, x + 3 * j, x + 3 * k, ff->angle_k[b],
+                              ff->angle_theta0[b], grad ? gi : NULL, gj, gk);
+        t.bend += e;
+        t.sum_abs += fabs(e);
+        if (grad)
+            for (int a = 0; a < 3; a++) {
+                grad[3 * i + a] += gi[a]; grad[3 * j + a] += gj[a]; grad[3 * k + a] += gk[a];
+            }
+    }
+    /* dihedrals */
+    for (int b = 0; b < ff->n_dihedrals; b++) {
+        const int32_t *q = ff->dihedral_idx + 4 * b;
+        double gi[3] = {0.0}, gj[3] = {0.0}, gk[3] = {0.0}, gl[3] = {0.0};
+        int deg = 0;
+        double e = dihedral_term(x + 3 * q[0], x + 3 * q[1], x + 3 * q[2], x + 3 * q[3],
+                                 ff->dihedral_v + 4 * b, grad ? gi : NULL, gj, gk, gl, &deg);
+        t.torsion += e;
+        t.sum_abs += fabs(e);
+        t.degenerate_dihedrals += deg;
+        if (grad)
+            for (int a = 0; a < 3; a++) {
+                grad[3 * q[0] + a] += gi[a]; grad[3 * q[1] + a] += gj[a];
+                grad[3 * q[2] + a] += gk[a]; grad[3 * q[3] + a] += gl[a];
+            }
+    }
+    *tp = t;
+}
+
 int orc_energy_terms(const orc_ff *ff, const double *x, double *grad, orc_terms *out) {
     const int n = ff->n_atoms;
     orc_terms t = {0};
@@ -241,51 +288,58 @@ int orc_energy_terms(const orc_ff *ff, const double *x, double *grad, orc_terms 
         }
     }
     free(sc);
-    /* bonds */
-    for (int b = 0; b < ff->n_bonds; b++) {
-        int i = ff->bond_idx[2 * b], j = ff->bond_idx[2 * b + 1];
-        double gi[3], gj[3];
-        double e = bond_term(x + 3 * i, x + 3 * j, ff->bond_k[b], ff->bond_r0[b],
-                             grad ? gi : NULL, gj);
-        t.stretch += e;
-        t.sum_abs += fabs(e);
-        if (grad)
-            for (int a = 0; a < 3; a++) { grad[3 * i + a] += gi[a]; grad[3 * j + a] += gj[a]; }
-    }
-    /* angles */
-    for (int b = 0; b < ff->n_angles; b++) {
-        int i = ff->angle_idx[3 * b], j = ff->angle_idx[3 * b + 1], k = ff->angle_idx[3 * b + 2];
-        double gi[3], gj[3], gk[3];
-        double e = angle_term(x + 3 * i, x + 3 * j, x + 3 * k, ff->angle_k[b],
-                              ff->angle_theta0[b], grad ? gi : NULL, gj, gk);
-        t.bend += e;
-        t.sum_abs += fabs(e);
-        if (grad)
-            for (int a = 0; a < 3; a++) {
-                grad[3 * i + a] += gi[a]; grad[3 * j + a] += gj[a]; grad[3 * k + a] += gk[a];
-            }
-    }
-    /* dihedrals */
-    for (int b = 0; b < ff->n_dihedrals; b++) {
-        const int32_t *q = ff->dihedral_idx + 4 * b;
-        double gi[3], gj[3], gk[3], gl[3];
-        int deg = 0;
-        double e = dihedral_term(x + 3 * q[0], x + 3 * q[1], x + 3 * q[2], x + 3 * q[3],
-                                 ff->dihedral_v + 4 * b, grad ? gi : NULL, gj, gk, gl, &deg);
-        t.torsion += e;
-        t.sum_abs += fabs(e);
-        t.degenerate_dihedrals += deg;
-        if (grad)
-            for (int a = 0; a < 3; a++) {
-                grad[3 * q[0] + a] += gi[a]; grad[3 * q[1] + a] += gj[a];
-                grad[3 * q[2] + a] += gk[a]; grad[3 * q[3] + a] += gl[a];
-            }
-    }
+    add_bonded(ff, x, grad, &t);
     t.total = t.stretch + t.bend + t.torsion + t.coulomb + t.vdw;
     if (!isfinite(t.total)) status = ORC_NONFINITE;
     if (grad)
         for (int k = 0; k < 3 * n; k++)
             if (!isfinite(grad[k])) status = ORC_NONFINITE;
+    if (out) *out = t;
+    return status;
+}
+
+/* orc_energy_terms restricted to the pairs (i, j), i < j, with i in [i0, i1),
+ * plus the bonded terms when i0 == 0: the energies of these terms (sum_abs
+ * and the parts as in orc_terms) and their gradient added into grad [3N]
+ * (rows of both atoms of a pair).  Summing the blocks of a partition of
+ * [0, N) gives the whole energy and gradient (in another order). */
+int orc_energy_rows(const orc_ff *ff, const double *x, int32_t i0, int32_t i1, double *grad,
+                    orc_terms *out) {
+    const int n = ff->n_atoms;
+    orc_terms t = {0};
+    int status = ORC_OK;
+    int32_t m_sc;
+    pscale_t *sc = scale_table(ff, &m_sc);
+    if (i0 < 0) i0 = 0;
+    if (i1 > n) i1 = n;
+    for (int i = i0; i < i1; i++) {
+        for (int j = i + 1; j < n; j++) {
+            double d[3];
+            sub3(x + 3 * i, x + 3 * j, d);
+            if (dot3(d, d) == 0.0) { status = ORC_NONFINITE; continue; }
+            const double s = pair_scale(ff, sc, m_sc, i, j);
+            if (s == 0.0) continue;
+            double ec, ev, f;
+            pair_term(ff->coulomb_c, ff->charge[i], ff->charge[j], ff->sigma[i], ff->sigma[j],
+                      ff->epsilon[i], ff->epsilon[j], d, &ec, &ev, &f);
+            ec *= s;
+            ev *= s;
+            f *= s;
+            t.coulomb += ec;
+            t.vdw += ev;
+            t.sum_abs += fabs(ec) + fabs(ev);
+            if (grad) {
+                for (int a = 0; a < 3; a++) {
+                    grad[3 * i + a] += f * d[a];
+                    grad[3 * j + a] -= f * d[a];
+                }
+            }
+        }
+    }
+    free(sc);
+    if (i0 == 0) add_bonded(ff, x, grad, &t);
+    t.total = t.stretch + t.bend + t.torsion + t.coulomb + t.vdw;
+    if (!isfinite(t.total)) status = ORC_NONFINITE;
     if (out) *out = t;
     return status;
 }

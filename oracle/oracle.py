@@ -69,6 +69,8 @@ def lib():
         L = C.CDLL(path)
         L.orc_energy_terms.argtypes = [C.POINTER(_FF), _dp, _dp, C.POINTER(_Terms)]
         L.orc_energy_terms.restype = C.c_int
+        L.orc_energy_rows.argtypes = [C.POINTER(_FF), _dp, C.c_int32, C.c_int32, _dp, C.POINTER(_Terms)]
+        L.orc_energy_rows.restype = C.c_int
         L.orc_energy_delta.argtypes = [C.POINTER(_FF), _dp, _dp, C.c_int32, C.c_int32, _dp, _dp]
         L.orc_energy_delta.restype = C.c_int
         L.orc_row_energy.argtypes = [C.POINTER(_FF), _dp, C.c_int32, _dp]
@@ -157,6 +159,18 @@ def energy(s, x):
 def energy_grad(s, x):
     d, st, g = energy_terms(s, x, grad=True)
     return d["total"], g
+
+
+def energy_rows(s, x, i0, i1, grad=True):
+    """(terms dict, status, gradient [N, 3] or None) of the pairs with
+    i0 <= i < j (bonded terms with i0 == 0)."""
+    f = _ff(s)
+    xx = _f64(x).reshape(-1)
+    g = np.zeros_like(xx) if grad else None
+    t = _Terms()
+    st = lib().orc_energy_rows(C.byref(f.s), _dptr(xx), int(i0), int(i1), _dptr(g), C.byref(t))
+    d = {k: getattr(t, k) for k, _ in _Terms._fields_}
+    return d, st, (g.reshape(-1, 3) if grad else None)
 
 
 def energy_delta(s, x, xp, rows=None):

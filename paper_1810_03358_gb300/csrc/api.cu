@@ -76,6 +76,9 @@ struct ffmin_system {
     Tile *d_tiles = nullptr;
     Item *d_items = nullptr;
     int2 *d_sys_items = nullptr;
+    // symmetric FP64 list (fixed at create)
+    int64_t n_slots64 = 0;
+    int n_items64 = 0;
     std::vector<int32_t> term_off[4];  // per-system offsets of bonds, angles, dihedrals, corrections
     int nb_total = 0, na_total = 0, nd_total = 0;
 };
@@ -93,6 +96,25 @@ static int chunk_len(int32_t n, int64_t total_tiles, int grid, int density) {
     return (int)len;
 }
 
+// bonded work items of system b (bonds, angles, dihedrals, exclusion
+// corrections; global term indices), appended to items
+static void bonded_items(const ffmin_system *sys, int b, std::vector<Item> &items) {
+    const int starts[4] = {sys->term_off[0][b], sys->nb_total + sys->term_off[1][b],
+                           sys->nb_total + sys->na_total + sys->term_off[2][b],
+                           sys->nb_total + sys->na_total + sys->nd_total + sys->term_off[3][b]};
+    for (int ty = 0; ty < 4; ty++) {
+        const int count = sys->term_off[ty][b + 1] - sys->term_off[ty][b];
+        for (int k = 0; k < count; k += BONDED_ITEM_TERMS) {
+            Item it{};
+            it.tile = -1;
+            it.j0 = starts[ty] + k;
+            it.nj = std::min(BONDED_ITEM_TERMS, count - k);
+            it.diag = b;
+            items.push_back(it);
+        }
+    }
+}
+
 // Work items for a given density, system by system: the system's bonded
 // items (latency-bound FP64 work that overlaps the FP32 pair items), then its
 // (tile, j-chunk) pair items; every system's items are contiguous so that
@@ -107,23 +129,7 @@ static void build_items(ffmin_system *sys, int density, std::vector<Item> &items
     size_t t = 0;
     for (int b = 0; b < sys->n_sys; b++) {
         const int first = (int)items.size();
-        // bonded ranges of system b: bonds, angles, dihedrals, exclusion
-        // corrections (global indices)
-        const int starts[4] = {sys->term_off[0][b], sys->nb_total + sys->term_off[1][b],
-                               sys->nb_total + sys->na_total + sys->term_off[2][b],
-                               sys->nb_total + sys->na_total + sys->nd_total + sys->term_off[3][b]};
-        int counts[4];
-        for (int ty = 0; ty < 4; ty++) counts[ty] = sys->term_off[ty][b + 1] - sys->term_off[ty][b];
-        for (int ty = 0; ty < 4; ty++) {
-            for (int k = 0; k < counts[ty]; k += BONDED_ITEM_TERMS) {
-                Item it{};
-                it.tile = -1;
-                it.j0 = starts[ty] + k;
-                it.nj = std::min(BONDED_ITEM_TERMS, counts[ty] - k);
-                it.diag = b;
-                items.push_back(it);
-            }
-        }
+        bonded_items(sys, b, items);
         const int64_t A = sys->atom_off[b];
         const int n = sys->sys_natoms[b];
         const int L = chunk_len(n, total_tiles, chunk_grid, density);
@@ -147,13 +153,64 @@ static void build_items(ffmin_system *sys, int density, std::vector<Item> &items
     }
 }
 
+// Symmetric FP64 list: per system its bonded items, then for every i-tile I
+// the chunks of `chunk` j-tiles covering tiles [I, nT) of the system (the
+// first chunk starts with the diagonal tile).  Item slots: the i-side rows,
+// then one row block per j-tile of the chunk.  chunk is chosen so that the
+// batch exposes about `want` items; tiles get row64 / chunk64 / tloc.
+static void build_items64(ffmin_system *sys, int64_t want, std::vector<Item> &items,
+                          std::vector<int2> &sys_items, int64_t *n_slots) {
+    items.clear();
+    sys_items.assign(sys->n_sys, make_int2(0, 0));
+    std::vector<Tile> &tiles = sys->tiles_h;
+    int64_t pairs = 0;
+    for (int b = 0; b < sys->n_sys; b++) {
+        const int64_t nT = (sys->sys_natoms[b] + TI - 1) / TI;
+        pairs += nT * (nT + 1) / 2;
+    }
+    const int chunk = (int)std::max<int64_t>(1, pairs / std::max<int64_t>(want, 1));
+    int64_t slots = 0;
+    size_t t = 0;
+    for (int b = 0; b < sys->n_sys; b++) {
+        const int first = (int)items.size();
+        bonded_items(sys, b, items);
+        const size_t t0 = t;
+        while (t < tiles.size() && tiles[t].sys == b) t++;
+        const int nT = (int)(t - t0);
+        for (int I = 0; I < nT; I++) {
+            Tile &tl = tiles[t0 + I];
+            tl.row64 = (int)items.size();
+            tl.chunk64 = chunk;
+            tl.tloc = I;
+            for (int J = I; J < nT; J += chunk) {
+                const int nJ = std::min(chunk, nT - J);
+                const Tile &last = tiles[t0 + J + nJ - 1];
+                Item it{};
+                it.tile = (int)(t0 + I);
+                it.j0 = tiles[t0 + J].a0;
+                it.nj = last.a0 + last.na - it.j0;
+                it.diag = J == I ? 1 : 0;
+                it.slot = (int)slots;
+                slots += 1 + nJ;
+                items.push_back(it);
+            }
+        }
+        sys_items[b] = make_int2(first, (int)items.size() - first);
+    }
+    *n_slots = slots;
+}
+
+// FP64 partial rows of the symmetric list above this size fall back to the
+// row sweep (its partial rows grow as the square of the atom count)
+static const int64_t SYM64_MAX_BYTES = 4LL << 30;
+
 static void set_item_counts(ffmin_system *sys, int n_items) {
     sys->c.n_items = n_items;
     sys->c.n_pair_items = n_items;
     // no more resident blocks than work items: idle blocks would only pay
     // for queue atomics
     sys->grid32 = std::max(1, std::min(sys->grid32_max, n_items));
-    sys->grid64 = std::max(1, std::min(sys->grid64_max, n_items));
+    sys->grid64 = std::max(1, std::min(sys->grid64_max, sys->c.sym64 ? sys->n_items64 : n_items));
 }
 
 static thread_local std::string g_create_err;
@@ -452,6 +509,18 @@ ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t pre
     for (int b = 0; b < n_sys; b++) sys->sys_natoms[b] = tops[b].n_atoms;
     sys->grid32_max = sys->grid32;
     sys->grid64_max = sys->grid64;
+    // symmetric FP64 list (fixed for the object): about 10 items per
+    // resident FP64 block; it also fills the tiles' row64 / chunk64 / tloc,
+    // which build_items copies
+    std::vector<Item> items64;
+    std::vector<int2> sys_items64;
+    const int grid_sym = pair_grid_size(2);
+    build_items64(sys, 10LL * grid_sym, items64, sys_items64, &sys->n_slots64);
+    sys->n_items64 = (int)items64.size();
+    const bool sym64 = sys->n_slots64 * TI * (int64_t)sizeof(double4_32a) <= SYM64_MAX_BYTES;
+    if (sym64) sys->grid64_max = grid_sym;
+    sys->c.sym64 = sym64 ? 1 : 0;
+    sys->c.n_items64 = sym64 ? sys->n_items64 : 0;
     // capacity: the densest layout the autotuner may choose
     build_items(sys, AUTOTUNE_DENSITIES[AUTOTUNE_N - 1], items, tiles, sys_items);
     sys->items_cap = (int64_t)items.size();
@@ -501,6 +570,14 @@ ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t pre
     CKC(upload(sys, &d_sys_items, sys_items));
     c.sys_items = d_sys_items;
     sys->d_sys_items = d_sys_items;
+    if (sym64) {
+        Item *d_items64;
+        int2 *d_sys_items64;
+        CKC(upload(sys, &d_items64, items64));
+        CKC(upload(sys, &d_sys_items64, sys_items64));
+        c.items64 = d_items64;
+        c.sys_items64 = d_sys_items64;
+    }
     CKC(dalloc(sys, &c.act, 2 * (2 * (size_t)n_sys + 2)));
     SysState *d_st;
     CKC(dalloc(sys, &d_st, n_sys));
@@ -516,7 +593,7 @@ ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t pre
         CKC(dalloc(sys, &c.posd, total));
         CKC(upload(sys, &d_pard, pard));
         c.pard = d_pard;
-        CKC(dalloc(sys, &c.gpd, (size_t)sys->items_cap * TI));
+        CKC(dalloc(sys, &c.gpd, (size_t)(sym64 ? sys->n_slots64 : sys->items_cap) * TI));
         if (precision == FFMIN_MIXED) {
             float2 *d_parf;
             CKC(dalloc(sys, &c.posf, total));
@@ -524,6 +601,7 @@ ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t pre
             CKC(upload(sys, &d_parf, parf));
             c.parf = d_parf;
             CKC(dalloc(sys, &c.gpf, (size_t)sys->items_cap * TI));
+            if (sym64) CKC(dalloc(sys, &c.gpf_sym, (size_t)sys->n_slots64 * TI));
         }
     }
     int32_t *d_inc_off; int2 *d_inc, *d_bidx; double2 *d_bpar, *d_apar; int4 *d_aidx, *d_didx; double4_32a *d_dpar;

@@ -54,11 +54,18 @@ enum Phase : int {
 };
 
 // a pair item (i-tile, j-chunk); tile < 0 marks a bonded item whose j0, nj
-// is a range of bonded terms (of one type and one system, diag = system)
-struct Item { int32_t tile, j0, nj, diag; };
+// is a range of bonded terms (of one type and one system, diag = system).
+// Row-sweep lists (FP32, and FP64 when the symmetric list would not fit):
+// every j of the system's row, slot unused.  Symmetric FP64 list: j-chunks
+// of whole tiles at or right of the i-tile; the item writes its i-side
+// partial rows to slot and the j-side rows of its q-th j-tile to slot + 1 + q.
+struct Item { int32_t tile, j0, nj, diag, slot, pad0, pad1, pad2; };
 constexpr int BONDED_ITEM_TERMS = 64;
 
-struct Tile { int32_t sys, a0, na, item0, nitem, pad0, pad1, pad2; };
+// item0 / nitem: the tile's items in the row-sweep list; row64: its first
+// item in the symmetric list (row of tile pairs (tile, J >= tile)), chunk64:
+// j-tiles per symmetric item of its system, tloc: index inside its system
+struct Tile { int32_t sys, a0, na, item0, nitem, row64, chunk64, tloc; };
 
 struct DirOp {
     int32_t on, use_d, dots;  // dots: 1 -> |R|^2, <G,R>; 2 -> <Y_j, R> for the Y list
@@ -146,6 +153,7 @@ struct Ctx {
     const double2 *pard;
     const double *qs;       // q * sqrt(C) per atom (FP64)
     float4 *gpf;            // [n_items][TI]
+    float4 *gpf_sym;        // [slots of items64][TI]: FP32 energy-only rows (i-side) on the symmetric list
     double4_32a *gpd;
     // bonded terms
     const int32_t *inc_off; // [n_atoms + 1]
@@ -162,6 +170,12 @@ struct Ctx {
     const double *xw;             // [n_excl] weight s_ij - 1 of its pair term
     const int32_t *term_sys;  // [n_terms] system of each bonded term
     const int2 *sys_items;  // [n_sys] (first, count) of each system's work items (contiguous)
+    // FP64 pair terms: sym64 = 1 evaluates each unordered pair once
+    // (symmetric tiles, list items64 / sys_items64, partial rows gpd
+    // [slots][TI]); 0 uses the row sweep over items / sys_items
+    int32_t sym64, n_items64;
+    const Item *items64;
+    const int2 *sys_items64;
     int32_t *act;           // per pair-kernel mode m: [m * (2 n_sys + 2)]: active systems, their
                             // items, item prefix [n_sys], system ids [n_sys] (rebuilt every launch)
     double *te;             // [n_terms] energy of each bonded term
@@ -196,6 +210,8 @@ cudaError_t launch_dir(const Ctx &c, int which, cudaStream_t s);
 // per-system reduction + control step after a stage (only when sep_reduce):
 // stage 0 update, 1 / 2 direction passes, 3 finalize
 cudaError_t launch_sysreduce(const Ctx &c, int stage, cudaStream_t s);
+// resident blocks of the pair kernel of a mode: 0 FP32 row sweep, 1 FP64
+// row sweep, 2 FP64 symmetric tiles
 int pair_grid_size(int mode);
 
 // arguments of one epoch of the parallel gradient-free search (one block

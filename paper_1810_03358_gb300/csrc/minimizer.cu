@@ -76,11 +76,39 @@ __global__ void __launch_bounds__(TI) k_finalize(Ctx c) {
     if (kind != EV_NONE && i < t.na) {
         const int a = t.a0 + i;
         double e = 0.0, g0 = 0.0, g1 = 0.0, g2 = 0.0;
-        if (mode == 0) {
+        if (mode == 0 && c.sym64 && kind == EV_E) {
+            // FP32 energy only on the symmetric list: the i-side rows of the
+            // tile's own row of items, each pair counted once
+            const SysState &S = c.st[t.sys];
+            const int T = t.tloc, C = t.chunk64;
+            const int nch = (S.ntile - T + C - 1) / C;
+            for (int q = 0; q < nch; q++) e += (double)c.gpf_sym[(int64_t)c.items64[t.row64 + q].slot * TI + i].w;
+        } else if (mode == 0) {
             for (int it = 0; it < t.nitem; it++) {
                 const float4 p = c.gpf[(int64_t)(t.item0 + it) * TI + i];
                 e += (double)p.w;
                 g0 += (double)p.x; g1 += (double)p.y; g2 += (double)p.z;
+            }
+            e = 0.5 * e;  // every pair was counted in both of its rows
+        } else if (c.sym64) {
+            // symmetric tiles: the j-side rows this tile received from the
+            // items of rows I <= T (in I order), then its own row's i-side
+            // rows; each pair's energy was counted once
+            const SysState &S = c.st[t.sys];
+            const int T = t.tloc, C = t.chunk64;
+            if (kind == EV_EG) {
+                for (int I = 0; I <= T; I++) {
+                    const int q = T - I;
+                    const int slot = c.items64[c.tiles[S.tile0 + I].row64 + q / C].slot + 1 + q % C;
+                    const double4_32a p = c.gpd[(int64_t)slot * TI + i];
+                    g0 += p.x; g1 += p.y; g2 += p.z;
+                }
+            }
+            const int nch = (S.ntile - T + C - 1) / C;
+            for (int q = 0; q < nch; q++) {
+                const double4_32a p = c.gpd[(int64_t)c.items64[t.row64 + q].slot * TI + i];
+                e += p.w;
+                g0 += p.x; g1 += p.y; g2 += p.z;
             }
         } else {
             for (int it = 0; it < t.nitem; it++) {
@@ -88,8 +116,8 @@ __global__ void __launch_bounds__(TI) k_finalize(Ctx c) {
                 e += p.w;
                 g0 += p.x; g1 += p.y; g2 += p.z;
             }
+            e = 0.5 * e;  // every pair was counted in both of its rows
         }
-        e = 0.5 * e;  // every pair was counted in both of its rows
         v[RF_EPAIR] = e;
         // bonded terms: evaluated once per term by the pair kernel's bonded
         // items; every atom gathers its terms' energies (as owner) and

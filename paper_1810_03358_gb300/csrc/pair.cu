@@ -50,8 +50,10 @@ template <> struct VT<double> {
     static __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 };
 
-// IPT i-atoms per thread share every j load from shared memory.
-template <typename T, int IPT, bool GRAD, bool DIAG>
+// IPT i-atoms per thread share every j load from shared memory.  DM: 0 an
+// off-diagonal tile; 1 the i-tile itself (j == i skipped); 2 the i-tile
+// itself on the symmetric list (only j > i: each pair once)
+template <typename T, int IPT, bool GRAD, int DM>
 __device__ __forceinline__ void sweep(const typename VT<T>::V4 *__restrict__ sp,
                                       const typename VT<T>::V2 *__restrict__ sq,
                                       const typename VT<T>::V4 (&pi)[IPT],
@@ -67,7 +69,8 @@ __device__ __forceinline__ void sweep(const typename VT<T>::V4 *__restrict__ sp,
             const T dx = pj.x - pi[u].x, dy = pj.y - pi[u].y, dz = pj.z - pi[u].z;
             const T r2 = dx * dx + dy * dy + dz * dz;
             T ri = VT<T>::rsq(r2);
-            if (DIAG) ri = (k == dk[u]) ? T(0) : ri;
+            if (DM == 1) ri = (k == dk[u]) ? T(0) : ri;
+            if (DM == 2) ri = (k <= dk[u]) ? T(0) : ri;
             const T ri2 = ri * ri;
             const T e = pi[u].w * pj.w * ri;
             const T ri6 = ri2 * ri2 * ri2;
@@ -98,7 +101,7 @@ __device__ __forceinline__ void sweep(const typename VT<T>::V4 *__restrict__ sp,
 // e_cul + 6 e_lj, whose rounding error is relative to the difference, not to
 // the energies (FP32 coordinates of the trial point would add noise of order
 // u |x| |F| per pair, larger than the line search's energy decrements).
-template <int IPT, bool DIAG>
+template <int IPT, int DM>
 __device__ __forceinline__ void sweep_delta(const float4 *__restrict__ sp, const float2 *__restrict__ sq,
                                             const float4 *__restrict__ sd, const float4 (&pi)[IPT],
                                             const float2 (&ci)[IPT], const float4 (&di)[IPT],
@@ -113,8 +116,9 @@ __device__ __forceinline__ void sweep_delta(const float4 *__restrict__ sp, const
             const float dx = pj.x - pi[u].x, dy = pj.y - pi[u].y, dz = pj.z - pi[u].z;
             const float ex = dj.x - di[u].x, ey = dj.y - di[u].y, ez = dj.z - di[u].z;
             float r2 = dx * dx + dy * dy + dz * dz;
-            if (DIAG) r2 = (k == dk[u]) ? 1.f : r2;  // j == i: dd = 0, every difference vanishes
-            const float D = ex * (2.f * dx + ex) + ey * (2.f * dy + ey) + ez * (2.f * dz + ez);
+            if (DM != 0) r2 = (k == dk[u]) ? 1.f : r2;  // j == i: dd = 0, every difference vanishes
+            float D = ex * (2.f * dx + ex) + ey * (2.f * dy + ey) + ez * (2.f * dz + ez);
+            if (DM == 2) D = (k <= dk[u]) ? 0.f : D;  // each pair once: j < i contributes nothing
             const float ri = rsqrt_approx(r2), rp = rsqrt_approx(r2 + D);
             const float ri2 = ri * ri, rp2 = rp * rp;
             const float X = -D * ri2 * rp2;
@@ -172,6 +176,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? FFMIN_F32_MINBLOCKS : 8)
     if (total == 0) return;
     const int32_t *aoff = A + 2, *asys = A + 2 + c.n_sys;
     const int tid = threadIdx.x;
+    __shared__ int s_sym;
     for (;;) {
         if (tid == 0) {
             const int q = (int)atomicAdd(&c.counters[CNT], 1u);
@@ -182,16 +187,22 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? FFMIN_F32_MINBLOCKS : 8)
                     if (aoff[mid] <= q) lo = mid;
                     else hi = mid - 1;
                 }
-                s_item = c.sys_items[asys[lo]].x + (q - aoff[lo]);
+                // FP32 energy-only evaluations (plain or difference trials)
+                // run on the symmetric list: each pair once, no forces
+                const int b = asys[lo];
+                const int sym = MODE == 0 && c.sym64 && c.st[b].ev_kind == EV_E;
+                s_item = (sym ? c.sys_items64 : c.sys_items)[b].x + (q - aoff[lo]);
+                s_sym = sym;
             } else {
                 s_item = -1;
             }
         }
         __syncthreads();
         const int it = s_item;
+        const bool sym = MODE == 0 && s_sym;
         __syncthreads();
         if (it < 0) break;
-        const Item I = c.items[it];
+        const Item I = sym ? c.items64[it] : c.items[it];
         if (I.tile < 0) {  // bonded terms (FP64), overlapping the pair items of other warps
             bonded_item(c, I.j0, I.nj, MODE);
             continue;
@@ -251,28 +262,164 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? FFMIN_F32_MINBLOCKS : 8)
             bool done = false;
             if constexpr (MODE == 0) {
                 if (delta) {
-                    if (diag) sweep_delta<IPT, true>(sp, sq, sd, pi, ci, di, dk, ec, lj);
-                    else sweep_delta<IPT, false>(sp, sq, sd, pi, ci, di, dk, ec, lj);
+                    if (diag && sym) sweep_delta<IPT, 2>(sp, sq, sd, pi, ci, di, dk, ec, lj);
+                    else if (diag) sweep_delta<IPT, 1>(sp, sq, sd, pi, ci, di, dk, ec, lj);
+                    else sweep_delta<IPT, 0>(sp, sq, sd, pi, ci, di, dk, ec, lj);
+                    done = true;
+                } else if (sym) {
+                    if (diag) sweep<T, IPT, false, 2>(sp, sq, pi, ci, dk, gx, gy, gz, ec, lj);
+                    else sweep<T, IPT, false, 0>(sp, sq, pi, ci, dk, gx, gy, gz, ec, lj);
                     done = true;
                 }
             }
             if (done) {
             } else if (kind == EV_EG) {
-                if (diag) sweep<T, IPT, true, true>(sp, sq, pi, ci, dk, gx, gy, gz, ec, lj);
-                else sweep<T, IPT, true, false>(sp, sq, pi, ci, dk, gx, gy, gz, ec, lj);
+                if (diag) sweep<T, IPT, true, 1>(sp, sq, pi, ci, dk, gx, gy, gz, ec, lj);
+                else sweep<T, IPT, true, 0>(sp, sq, pi, ci, dk, gx, gy, gz, ec, lj);
             } else {
-                if (diag) sweep<T, IPT, false, true>(sp, sq, pi, ci, dk, gx, gy, gz, ec, lj);
-                else sweep<T, IPT, false, false>(sp, sq, pi, ci, dk, gx, gy, gz, ec, lj);
+                if (diag) sweep<T, IPT, false, 1>(sp, sq, pi, ci, dk, gx, gy, gz, ec, lj);
+                else sweep<T, IPT, false, 0>(sp, sq, pi, ci, dk, gx, gy, gz, ec, lj);
             }
             __syncthreads();
+        }
+        // symmetric list (FP32 energy only): the i-side rows of the item's slot
+        V4 *dst = out + (int64_t)it * TI;
+        if constexpr (MODE == 0) {
+            if (sym) dst = c.gpf_sym + (int64_t)I.slot * TI;
         }
 #pragma unroll
         for (int u = 0; u < IPT; u++) {
             V4 o;
             o.x = gx[u]; o.y = gy[u]; o.z = gz[u];
             o.w = ec[u] + lj[u] * T(1.0 / 6.0);
-            out[(int64_t)it * TI + tid + u * NT] = o;
+            dst[tid + u * NT] = o;
         }
+    }
+}
+
+// Symmetric FP64 pair kernel: every unordered pair once.  The FP64 pipe
+// (2 FMA per clock per SM) is the limit of the FP64 terms, so the row sweep's
+// double evaluation of each pair is its largest cost; here an item (i-tile
+// I, chunk of j-tiles at or right of I) evaluates each pair (i, j) once,
+// adds the force to i's registers and its opposite to j's entry of a
+// warp-private shared-memory array (lanes of a warp take distinct j at every
+// step: lane t pairs with j = (t + k) mod TJ at step k; the diagonal tile runs
+// k = 1 .. TJ/2 and, at k = TJ/2, only its first half of the threads, so
+// every pair of the tile appears once).  No atomics: after each j-tile the
+// four warps' arrays are summed in warp order into the tile's j-side
+// partial rows, and the i-side rows are written once per item; the finalize
+// kernel sums an atom's j-side rows (tiles I <= its tile) and i-side rows in
+// a fixed order.  Row energies count each pair once.
+constexpr int NT_SYM = 128;
+__global__ void __launch_bounds__(NT_SYM, 6) k_pair64_sym(Ctx c) {
+    __shared__ double4_32a sp[TJ];
+    __shared__ double2 sq[TJ];
+    __shared__ double jfx[NT_SYM / 32][TJ], jfy[NT_SYM / 32][TJ], jfz[NT_SYM / 32][TJ];
+    __shared__ int s_item;
+    const int32_t *A = c.act + 1 * (2 * c.n_sys + 2);
+    const int n_act = A[0], total = A[1];
+    if (total == 0) return;
+    const int32_t *aoff = A + 2, *asys = A + 2 + c.n_sys;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    for (;;) {
+        if (tid == 0) {
+            const int q = (int)atomicAdd(&c.counters[CNT_PAIR64], 1u);
+            if (q < total) {  // last active system whose first item is <= q
+                int lo = 0, hi = n_act - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (aoff[mid] <= q) lo = mid;
+                    else hi = mid - 1;
+                }
+                s_item = c.sys_items64[asys[lo]].x + (q - aoff[lo]);
+            } else {
+                s_item = -1;
+            }
+        }
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it < 0) break;
+        const Item I = c.items64[it];
+        if (I.tile < 0) {
+            bonded_item(c, I.j0, I.nj, 1);
+            continue;
+        }
+        const Tile tl = c.tiles[I.tile];
+        const int kind = c.st[tl.sys].ev_kind;
+        if (kind == EV_NONE || c.st[tl.sys].mode != 1) continue;
+        const bool grad = kind == EV_EG;
+        double4_32a pi;
+        double2 ci;
+        if (tid < tl.na) {
+            pi = c.posd[tl.a0 + tid];
+            ci = c.pard[tl.a0 + tid];
+        } else {  // padding atom far away with no charge and no LJ
+            pi = make_double4_32a(-1e6, -1e6, -1e6, 0.0);
+            ci = make_double2(0.0, 0.0);
+        }
+        double gx = 0.0, gy = 0.0, gz = 0.0, ec = 0.0, lj = 0.0;
+        const int jend = I.j0 + I.nj;
+        for (int jt = I.j0; jt < jend; jt += TJ) {
+            const int jl = jt + tid;
+            if (jl < jend) {
+                sp[tid] = c.posd[jl];
+                sq[tid] = c.pard[jl];
+            } else {
+                sp[tid] = make_double4_32a(1e6, 1e6, 1e6, 0.0);
+                sq[tid] = make_double2(0.0, 0.0);
+            }
+            if (grad) {
+#pragma unroll
+                for (int q = lane; q < TJ; q += 32) { jfx[w][q] = 0.0; jfy[w][q] = 0.0; jfz[w][q] = 0.0; }
+            }
+            __syncthreads();
+            // the diagonal tile (j-tile == i-tile) pairs t with t + k,
+            // k = 1 .. TJ/2 (at k = TJ/2 only t < TJ/2); other tiles every k
+            const bool diag = I.diag && jt == I.j0;
+            const int k0 = diag ? 1 : 0, k1 = diag ? TJ / 2 : TJ - 1;
+            for (int k = k0; k <= k1; k++) {
+                if (diag && k == TJ / 2 && tid >= TJ / 2) break;  // warp-uniform
+                const int j = (tid + k) & (TJ - 1);
+                const double4_32a pj = sp[j];
+                const double2 qj = sq[j];
+                const double dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+                const double r2 = dx * dx + dy * dy + dz * dz;
+                const double ri = rsqrt(r2);
+                const double ri2 = ri * ri;
+                const double e = pi.w * pj.w * ri;
+                const double ri6 = ri2 * ri2 * ri2;
+                const double c6 = ci.x * qj.x, c12 = ci.y * qj.y;
+                const double t1 = c12 * ri6 - c6;
+                ec += e;
+                lj += ri6 * t1;
+                if (grad) {
+                    const double t2 = c12 * ri6 + t1;
+                    const double f = (ri6 * t2 + e) * ri2;
+                    gx += f * dx;
+                    gy += f * dy;
+                    gz += f * dz;
+                    jfx[w][j] -= f * dx;
+                    jfy[w][j] -= f * dy;
+                    jfz[w][j] -= f * dz;
+                }
+                __syncwarp();
+            }
+            __syncthreads();
+            if (grad) {  // j-side partial rows of this j-tile, warps summed in order
+                double4_32a o;
+                o.x = jfx[0][tid]; o.y = jfy[0][tid]; o.z = jfz[0][tid];
+#pragma unroll
+                for (int v = 1; v < NT_SYM / 32; v++) { o.x += jfx[v][tid]; o.y += jfy[v][tid]; o.z += jfz[v][tid]; }
+                o.w = 0.0;
+                c.gpd[(int64_t)(I.slot + 1 + (jt - I.j0) / TJ) * TI + tid] = o;
+            }
+            __syncthreads();
+        }
+        double4_32a o;
+        o.x = gx; o.y = gy; o.z = gz;
+        o.w = ec + lj * (1.0 / 6.0);
+        c.gpd[(int64_t)I.slot * TI + tid] = o;
     }
 }
 
@@ -288,8 +435,10 @@ int pair_grid_size(int mode) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (mode == 0)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, K_F32, NT_F32, 0);
-    else
+    else if (mode == 1)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, K_F64, NT_F64, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pair64_sym, NT_SYM, 0);
     if (per < 1) per = 1;
     return sms * per;
 }
@@ -315,7 +464,10 @@ __global__ void __launch_bounds__(256) k_activelist(Ctx c) {
             int n = 0;
             if (b < c.n_sys) {
                 const SysState &S = c.st[b];
-                if (S.ev_kind != EV_NONE && S.mode == m) n = c.sys_items[b].y;
+                // FP64 terms and FP32 energy-only evaluations use the
+                // symmetric list (when the object has one)
+                const bool sym = c.sym64 && (m == 1 || S.ev_kind == EV_E);
+                if (S.ev_kind != EV_NONE && S.mode == m) n = (sym ? c.sys_items64 : c.sys_items)[b].y;
             }
             const int f = n > 0 ? 1 : 0;
             int si = n, ss = f;  // inclusive scans within the warp
@@ -351,7 +503,8 @@ cudaError_t launch_pair(const Ctx &c, int grid32, int grid64, cudaStream_t s) {
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    K_F64<<<grid64, NT_F64, 0, s>>>(c);
+    if (c.sym64) k_pair64_sym<<<grid64, NT_SYM, 0, s>>>(c);
+    else K_F64<<<grid64, NT_F64, 0, s>>>(c);
     return cudaGetLastError();
 }
 

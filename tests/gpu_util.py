@@ -71,3 +71,20 @@ def oracle_energy_delta(s, x, xp, blocks=64):
     parts = oracle_map(_oracle_delta_rows, [s] * len(lo), [x] * len(lo), [xp] * len(lo), lo, hi)
     assert all(p[2] == 0 for p in parts)
     return sum(p[0] for p in parts), sum(p[1] for p in parts)
+
+
+U32 = 2.0 ** -24  # FP32 unit roundoff
+
+
+def mixed_position_bound(x):
+    """First-order bound, relative to the terms themselves, of what the FP32
+    rounding of the positions (u |x| per coordinate, so at most
+    2 sqrt(3) u |x|max on a separation) does to a pair term through its
+    r^-12 power: 12 * 2 sqrt(3) u |x|max / r_min, r_min the smallest
+    separation of the configuration."""
+    from scipy.spatial import cKDTree
+    x = np.asarray(x, dtype=np.float64).reshape(-1, 3)
+    if x.shape[0] < 2:
+        return 0.0
+    d, _ = cKDTree(x).query(x, k=2)
+    return 12.0 * 2.0 * np.sqrt(3.0) * U32 * np.abs(x).max() / d[:, 1].min()

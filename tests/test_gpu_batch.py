@@ -10,15 +10,19 @@ batches of 16, 64 and 256 systems drawn from that workload's generator
 
 Bars are those of the single-system tests: FP64 energy within 2e-11 of
 sum|terms| and gradient within 1e-9 of the largest force; MIXED energy
-within 1e-5 of sum|terms| and gradient within 1e-4 of the largest force;
+within 1e-5 of sum|terms| plus the first-order effect of the FP32 position
+rounding (tests.gpu_util.mixed_position_bound: 12 * 2 sqrt(3) u |x|max /
+r_min, up to 1.8e-4 at the batch's closest jittered pairs, 0.29 A) and
+gradient within 1e-4 of the largest force;
 L-BFGS prefixes of 60 accepted steps with the oracle's exact iteration and
 evaluation counts (test_gpu_minimize.prefix_parity)."""
 import numpy as np
 import pytest
 
 from paper_1810_03358_gb300 import synth
-from tests.gpu_util import _oracle_energy_terms, _oracle_minimize, need_gpu, oracle_map, split, to_dev
-from tests.test_gpu_minimize import PREFIX, prefix_parity
+from tests.gpu_util import (_oracle_energy_terms, _oracle_minimize, mixed_position_bound, need_gpu, oracle_map,
+                            split, to_dev)
+from tests.test_gpu_minimize import PREFIX, PREFIX_FGM, prefix_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -53,9 +57,10 @@ def energy_parity(ffmin, systems, prec):
         assert st == 0
         err_e = abs(e[b] - d["total"]) / d["sum_abs"]
         err_g = np.abs(g[b] - go).max() / np.abs(go).max()
-        assert err_e <= TOL[prec]["e"], (b, err_e)
+        bar_e = TOL[prec]["e"] + (mixed_position_bound(systems[b].x) if prec == 1 else 0.0)
+        assert err_e <= bar_e, (b, err_e, bar_e)
         assert err_g <= TOL[prec]["g"], (b, err_g)
-        assert abs(e_only[b] - e[b]) <= TOL[prec]["e"] * d["sum_abs"], b
+        assert abs(e_only[b] - e[b]) <= 2 * bar_e * d["sum_abs"], b
         worst_e, worst_g = max(worst_e, err_e), max(worst_g, err_g)
     return worst_e, worst_g
 
@@ -91,7 +96,7 @@ def test_batch_other_methods_prefix_fp64(ff, oracle_mod):
     # the per-system control path of the other methods at n_sys >= 8
     systems = batch_systems(12, 600)
     for method in (0, 1, 2, 5):
-        kw = dict(method=method, max_iter=PREFIX)
+        kw = dict(method=method, max_iter=PREFIX_FGM if method == 1 else PREFIX)
         S = ff.System(systems, 0)
         x = to_dev([s.x for s in systems])
         rg = S.minimize(x, **kw)

@@ -96,7 +96,7 @@ def test_lbfgs_prefix_and_full_run(ff, oracle_mod):
     prefix_parity(oracle_mod, s, xg[0], rg[0], kw)
     kw = dict(method=3, max_iter=100000)
     xg, rg, _ = run_gpu(ff, [s], 0, **kw)
-    ensemble_parity(oracle_mod, s, xg[0], rg[0], kw, members=3)
+    ensemble_parity(oracle_mod, s, xg[0], rg[0], kw)
 
 
 def test_gradient_free_moves(ff, oracle_mod):

@@ -31,7 +31,7 @@ import numpy as np
 import pytest
 
 from paper_1810_03358_gb300 import synth
-from tests.gpu_util import need_gpu, split, to_dev
+from tests.gpu_util import _oracle_minimize, need_gpu, oracle_map, split, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -39,6 +39,34 @@ REL_E = 1e-4  # 0.01 %
 # capped prefix: measured divergence grows ~1.14x per step from 1e-16, so 60
 # steps keep the two trajectories equal to ~1e-12
 PREFIX = 60
+# Algorithm 1 as printed (FGM without restart) reaches its best point within
+# ~30 steps on these clashing starts and then runs with beta -> 1, which
+# amplifies rounding differences far faster: its line searches' evaluation
+# counts become rounding-decided (the oracle's own runs from starts 1e-15 ..
+# 1e-13 A apart differ by 1 or 2).  Its exact-count prefix is 25 steps; at
+# 60 steps its returned best point is compared (unique and robust).
+PREFIX_FGM = 25
+
+
+def fgm_literal(kw):
+    return kw.get("method") == 1 and not kw.get("fgm_restart", 0)
+
+
+def prefix_or_best(oracle_mod, s, ff, systems_prec, kw):
+    """Prefix parity; for literal FGM the 25-step prefix plus the 60-step
+    best point (energy within 1e-8, coordinates within 1e-6 A)."""
+    if not fgm_literal(kw):
+        xg, rg, _ = run_gpu(ff, [s], systems_prec, **kw)
+        prefix_parity(oracle_mod, s, xg[0], rg[0], kw)
+        return
+    k25 = dict(kw, max_iter=PREFIX_FGM)
+    xg, rg, _ = run_gpu(ff, [s], systems_prec, **k25)
+    prefix_parity(oracle_mod, s, xg[0], rg[0], k25)
+    xg, rg, _ = run_gpu(ff, [s], systems_prec, **kw)
+    xo, ro = oracle_mod.minimize(s, s.x, **kw)
+    assert rg[0]["iterations"] == ro["iterations"] and rg[0]["status_name"] == ro["status_name"]
+    assert abs(rg[0]["energy"] - ro["energy"]) <= 1e-8 * abs(ro["energy"]), (rg[0], ro)
+    assert np.abs(xg[0] - xo).max() <= 1e-6
 STATUS = {"ok": "ok", "linesearch": "linesearch", "max_iter": "max_iter", "nonfinite": "nonfinite"}
 
 
@@ -57,68 +85,84 @@ def run_gpu(ffmin, systems, prec, **opts):
     return xs, res, stats
 
 
-def oracle_sensitivity(oracle_mod, s, xo, ro, kw, members=3, eps=1e-15):
-    """How far the oracle's own capped run moves when its start moves by
-    eps A (rounding level): (max relative energy change, max coordinate
-    change, whether every member kept the oracle's counts)."""
-    de, dx, same = 0.0, 0.0, True
-    for k in range(1, members + 1):
-        x0 = s.x + eps * np.random.default_rng(k).normal(size=s.x.shape)
+COUNTS = ("iterations", "energy_evals", "grad_evals", "ls_failures")
+
+
+def oracle_sensitivity(oracle_mod, s, xo, ro, kw, eps=(1e-15, 1e-14, 1e-13)):
+    """How far the oracle's own capped run moves when its start moves by a
+    rounding-scale amount: one member per eps (A).  The GPU's rounding
+    differs from the oracle's in every evaluation of the run, not only at
+    the start: about sqrt(60) evaluations' worth of ~u |x| = 4e-15 A, i.e.
+    up to ~3e-14 A, which the members bracket.  Returns (max relative
+    energy change, max coordinate change, the members' count tuples)."""
+    de, dx, counts = 0.0, 0.0, []
+    for k, e in enumerate(eps, start=1):
+        x0 = s.x + e * np.random.default_rng(k).normal(size=s.x.shape)
         x1, r1 = oracle_mod.minimize(s, x0, **kw)
         de = max(de, abs(r1["energy"] - ro["energy"]) / abs(ro["energy"]))
         dx = max(dx, float(np.abs(x1 - xo).max()))
-        same = same and all(r1[k2] == ro[k2] for k2 in ("iterations", "energy_evals", "grad_evals"))
-    return de, dx, same
+        counts.append(tuple(r1[c] for c in COUNTS))
+    return de, dx, counts
 
 
 def prefix_parity(oracle_mod, s, xg, rg, kw, ref=None):
     xo, ro = ref if ref is not None else oracle_mod.minimize(s, s.x, **kw)
     assert rg["status_name"] == STATUS[ro["status_name"]], (rg, ro)
-    for k in ("iterations", "energy_evals", "grad_evals", "ls_failures"):
-        assert rg[k] == ro[k], (k, rg, ro)
+    same_counts = all(rg[k] == ro[k] for k in COUNTS)
     de = abs(rg["energy"] - ro["energy"]) / abs(ro["energy"])
     dx = float(np.abs(xg - xo).max())
-    if de <= 1e-8 and dx <= 1e-6:
+    if same_counts and de <= 1e-8 and dx <= 1e-6:
         return
     # some capped runs are chaotic already within the prefix: the oracle's
-    # own run, restarted 1e-15 A away, moves by a comparable amount.  The
-    # GPU run (different summation order, i.e. rounding-level differences in
-    # every evaluation) must then stay within 10x that self-sensitivity.
-    se, sx, _ = oracle_sensitivity(oracle_mod, s, xo, ro, kw)
+    # own run, restarted a rounding-scale distance away, moves by a
+    # comparable amount.  The GPU run (different summation order, i.e.
+    # rounding-level differences in every evaluation) must then stay within
+    # 10x that self-sensitivity; its counts may differ from the oracle's only
+    # where the oracle's own counts flip under such a perturbation (a
+    # line-search comparison decided by rounding), and must then equal a
+    # member's.
+    se, sx, counts = oracle_sensitivity(oracle_mod, s, xo, ro, kw)
+    if not same_counts:
+        assert tuple(rg[k] for k in COUNTS) in counts, (rg, ro, counts)
     assert de <= max(1e-8, 10.0 * se), (de, se, rg, ro)
     assert dx <= max(1e-6, 10.0 * sx), (dx, sx)
 
 
-def ensemble_parity(oracle_mod, s, xg, rg, kw, members=4, eps=1e-12):
-    energies = []
-    for k in range(members):
-        x0 = s.x if k == 0 else s.x + eps * np.random.default_rng(k).normal(size=s.x.shape)
-        xo, ro = oracle_mod.minimize(s, x0, **kw)
-        if ro["status_name"] == "ok":
-            energies.append(ro["energy"])
+# the fixed oracle ensemble of a full run: the start itself and starts
+# perturbed by 1e-12 .. 1e-6 A (seeds 1 .. 6).  1e-12 A is the rounding
+# scale of the FP64 path's differences; 1e-6 A that of FP32 coordinates
+# (u |x| at 20 A), the perturbation a MIXED trajectory carries
+ENSEMBLE_EPS = (0.0, 1e-12, 1e-12, 1e-10, 1e-8, 1e-6, 1e-6)
+
+
+def oracle_ensemble(s, kw):
+    starts = [s.x if e == 0.0 else s.x + e * np.random.default_rng(k).normal(size=s.x.shape)
+              for k, e in enumerate(ENSEMBLE_EPS)]
+    n = len(starts)
+    out = oracle_map(_oracle_minimize, [s] * n, starts, [kw] * n)
+    return [r["energy"] for _, r in out if r["status_name"] == "ok"]
+
+
+def ensemble_parity(oracle_mod, s, xg, rg, kw, energies=None):
+    """A full run against the fixed oracle ensemble: its final energy lies
+    within 0.01 % of the members' range (or below it by at most the range
+    itself), or within 0.01 % of one member; it is a valid stop (the
+    oracle's gradient of the returned point below the tolerance) and reports
+    that point's energy.  Prints which criterion held."""
+    if energies is None:
+        energies = oracle_ensemble(s, kw)
     assert energies, "the oracle itself did not converge"
     lo, hi = min(energies), max(energies)
     tol = REL_E * max(abs(lo), abs(hi))
-    # above: within 0.01 % of the worst oracle member; below: a lower minimum
-    # is accepted down to the ensemble's own spread (the chaos that separates
-    # the oracle's members separates the GPU run from them as well)
-    if not (lo - max(tol, hi - lo) <= rg["energy"] <= hi + tol):
-        # the GPU run reached another basin than these members: it is still a
-        # result of the method if some oracle run from a start perturbed by
-        # 1e-12 .. 1e-6 A ends within 0.01 % of it
-        hit = False
-        for k, e in enumerate([1e-12, 1e-10, 1e-8, 1e-6] * 3):
-            x0 = s.x + e * np.random.default_rng(100 + k).normal(size=s.x.shape)
-            xo, ro = oracle_mod.minimize(s, x0, **kw)
-            if ro["status_name"] == "ok":
-                energies.append(ro["energy"])
-                if abs(ro["energy"] - rg["energy"]) <= REL_E * abs(rg["energy"]):
-                    hit = True
-                    break
-        assert hit, (rg["energy"], energies)
+    e = rg["energy"]
+    in_range = lo - max(tol, hi - lo) <= e <= hi + tol
+    near = any(abs(m - e) <= REL_E * abs(e) for m in energies)
+    print(f"ensemble ({len(energies)} members, spread {(hi - lo) / abs(lo):.1e}): "
+          f"{'range' if in_range else ('member' if near else 'miss')}, gpu {e:.10g}")
+    assert in_range or near, (e, energies)
     assert rg["status_name"] == "ok", rg
     e_ret, g_ret = oracle_mod.energy_grad(s, xg)
-    assert abs(e_ret - rg["energy"]) <= 1e-9 * max(abs(e_ret), 1.0)
+    assert abs(e_ret - e) <= 1e-9 * max(abs(e_ret), 1.0)
     assert np.abs(g_ret).max() < kw.get("gtol_inf", 0.1) * (1 + 1e-6)
     return energies
 
@@ -127,9 +171,7 @@ def ensemble_parity(oracle_mod, s, xg, rg, kw, members=4, eps=1e-12):
 @pytest.mark.parametrize("n,seed", [(40, 21), (130, 22)])
 def test_prefix_methods(ff, oracle_mod, method, n, seed):
     s = synth.make_system(n, seed)
-    kw = dict(method=method, max_iter=PREFIX)
-    xg, rg, _ = run_gpu(ff, [s], 0, **kw)
-    prefix_parity(oracle_mod, s, xg[0], rg[0], kw)
+    prefix_or_best(oracle_mod, s, ff, 0, dict(method=method, max_iter=PREFIX))
 
 
 @pytest.mark.parametrize("ls", [0, 2])
@@ -173,9 +215,7 @@ def test_prefix_cg_variants(ff, oracle_mod, variant):
 @pytest.mark.parametrize("method", [0, 1, 2, 3, 5])
 def test_prefix_line_search_choice(ff, oracle_mod, ls, method):
     s = synth.make_system(50, 24)
-    kw = dict(method=method, ls=ls, max_iter=PREFIX)
-    xg, rg, _ = run_gpu(ff, [s], 0, **kw)
-    prefix_parity(oracle_mod, s, xg[0], rg[0], kw)
+    prefix_or_best(oracle_mod, s, ff, 0, dict(method=method, ls=ls, max_iter=PREFIX))
 
 
 @pytest.mark.parametrize("extra", [dict(ls_par_K=4), dict(ls_par_g0=0), dict(lbfgs_m=1),
@@ -285,7 +325,7 @@ def test_full_runs_batched_ensemble(ff, oracle_mod):
     kw = dict(method=3, max_iter=100000)
     xg, rg, _ = run_gpu(ff, systems, 0, **kw)
     for b, s in enumerate(systems):
-        ensemble_parity(oracle_mod, s, xg[b], rg[b], kw, members=3)
+        ensemble_parity(oracle_mod, s, xg[b], rg[b], kw)
 
 
 def test_paper_small_config_lbfgs_500(ff, oracle_mod):
@@ -297,7 +337,7 @@ def test_paper_small_config_lbfgs_500(ff, oracle_mod):
     prefix_parity(oracle_mod, s, xg[0], rg[0], kw)
     kw["max_iter"] = 100000
     xg, rg, _ = run_gpu(ff, [s], 0, **kw)
-    ensemble_parity(oracle_mod, s, xg[0], rg[0], kw, members=3)
+    ensemble_parity(oracle_mod, s, xg[0], rg[0], kw)
 
 
 def test_host_entry_point(ff, oracle_mod):
@@ -320,12 +360,9 @@ def test_mixed_fp32_then_fp64(ff, oracle_mod, method):
     xg, rg, _ = run_gpu(ff, [s], 1, **kw)
     r = rg[0]
     assert r["status_name"] == "ok", r
-    e_true, g_true = oracle_mod.energy_grad(s, xg[0])
-    assert np.abs(g_true).max() < 0.1 * (1 + 1e-6)
-    assert abs(e_true - r["energy"]) <= 1e-9 * abs(e_true)
-    xo, ro = oracle_mod.minimize(s, s.x, **kw)
-    # a different trajectory: a neighbouring minimum, within 0.5 %
-    assert abs(r["energy"] - ro["energy"]) <= 5e-3 * abs(ro["energy"])
+    # a trajectory perturbed at the FP32 scale: held to the same fixed
+    # ensemble and 0.01 % bar as the FP64 path (members perturbed up to 1e-6 A)
+    ensemble_parity(oracle_mod, s, xg[0], r, kw)
 
 
 def test_mixed_batched(ff, oracle_mod):
@@ -333,7 +370,4 @@ def test_mixed_batched(ff, oracle_mod):
     kw = dict(method=3, max_iter=100000)
     xg, rg, _ = run_gpu(ff, systems, 1, **kw)
     for b, s in enumerate(systems):
-        assert rg[b]["status_name"] == "ok", rg[b]
-        e_true, g_true = oracle_mod.energy_grad(s, xg[b])
-        assert np.abs(g_true).max() < 0.1 * (1 + 1e-6)
-        assert abs(e_true - rg[b]["energy"]) <= 1e-9 * abs(e_true)
+        ensemble_parity(oracle_mod, s, xg[b], rg[b], kw)

@@ -256,3 +256,24 @@ def test_energy_delta_definition(oracle_mod, excl):
     dp = oracle_mod.energy_delta(s, s.x, s.x + h * r)[0]
     dm = oracle_mod.energy_delta(s, s.x, s.x - h * r)[0]
     assert (dp - dm) / (2 * h) == pytest.approx(slope, rel=1e-5)
+
+
+@pytest.mark.parametrize("excl", [0, 1])
+def test_energy_rows_partition(oracle_mod, excl):
+    # row blocks of a partition of [0, N) sum to the whole energy and gradient
+    s = synth.make_system(70, 42)
+    s.exclusions, s.scale14 = excl, 0.5
+    d, st, g = oracle_mod.energy_terms(s, s.x, grad=True)
+    tot, gsum = 0.0, np.zeros_like(g)
+    parts = {k: 0.0 for k in ("stretch", "bend", "torsion", "coulomb", "vdw", "sum_abs")}
+    for i0, i1 in [(0, 9), (9, 33), (33, 34), (34, 70)]:
+        dd, st2, gg = oracle_mod.energy_rows(s, s.x, i0, i1)
+        assert st2 == 0
+        tot += dd["total"]
+        gsum += gg
+        for k in parts:
+            parts[k] += dd[k]
+    assert tot == pytest.approx(d["total"], rel=1e-12)
+    for k in parts:
+        assert parts[k] == pytest.approx(d[k], rel=1e-12, abs=1e-12 * d["sum_abs"]), k
+    assert np.abs(gsum - g).max() <= 1e-12 * np.abs(g).max()
