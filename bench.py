@@ -50,6 +50,12 @@ FLOPS_UNIQUE_EG = 35.0
 FLOPS_UNIQUE_E = 23.0
 FLOPS_PER_PAIR_EG = 32.0
 FLOPS_PER_PAIR_E = 21.0
+# hardware flops per unique pair of each kernel form: the FP64 symmetric
+# tiles evaluate a pair once and add its force to both atoms (32 + 6); the
+# FP32 E + grad row sweep evaluates it twice (2 x 32); the energy-only and
+# difference-trial forms run on the symmetric tiles once (21; ~40 for the
+# exact-difference identities)
+HW_SYM_EG, HW_SYM_E, HW_ROW_EG, HW_DELTA = 38.0, 21.0, 64.0, 40.0
 # ALU peaks derived from unit counts at the maximum SM clock: FP32 152 SMs x
 # 128 lanes x 2 flops; FP64 152 SMs x 2 FMA per clock x 2 flops (the GB300
 # nominal 1.25 TFLOP/s at 2,070 MHz)
@@ -284,21 +290,29 @@ def bench_gpu(args):
     fp32_probe = ffmin.ffmin_alu_peak(ffmin.FFMIN_MIXED, reps=20)
     fp64_probe = ffmin.ffmin_alu_peak(ffmin.FFMIN_FP64, reps=20)
 
+    unique = N_ATOMS * (N_ATOMS - 1) // 2
+
     def roof(ms, unique_flops, hw_flops, peak):
         """Algorithmic FLOP/s (unique pairs x the per-pair count) and the
-        row sweep's hardware FLOP/s (evaluated pairs), both against peak."""
-        unique = N_ATOMS * (N_ATOMS - 1) // 2
+        kernel's executed FLOP/s (its own per-pair formula), against peak."""
         achieved = unique_flops * unique / (ms / 1e3) / 1e12
-        hw = hw_flops * 2 * unique / (ms / 1e3) / 1e12
+        hw = hw_flops * unique / (ms / 1e3) / 1e12
         return {"achieved": achieved, "frac": achieved / peak, "hw_achieved": hw, "hw_frac": hw / peak,
                 "ms_per_launch": ms, "unique_pairs_per_s": unique / (ms / 1e3)}
 
-    r64 = roof(ms_pair, FLOPS_UNIQUE_EG, FLOPS_PER_PAIR_EG, fp64_derived)
-    r64e = roof(ms_pair_e, FLOPS_UNIQUE_E, FLOPS_PER_PAIR_E, fp64_derived)
-    r32 = roof(ms_pair32, FLOPS_UNIQUE_EG, FLOPS_PER_PAIR_EG, fp32_derived)
-    r32e = roof(ms_pair32_e, FLOPS_UNIQUE_E, FLOPS_PER_PAIR_E, fp32_derived)
-    r32d = roof(ms_pair32_d, FLOPS_UNIQUE_E, FLOPS_PER_PAIR_E, fp32_derived)
+    r64 = roof(ms_pair, FLOPS_UNIQUE_EG, HW_SYM_EG, fp64_derived)
+    r64e = roof(ms_pair_e, FLOPS_UNIQUE_E, HW_SYM_E, fp64_derived)
+    r32 = roof(ms_pair32, FLOPS_UNIQUE_EG, HW_ROW_EG, fp32_derived)
+    r32e = roof(ms_pair32_e, FLOPS_UNIQUE_E, HW_SYM_E, fp32_derived)
+    r32d = roof(ms_pair32_d, FLOPS_UNIQUE_E, HW_DELTA, fp32_derived)
     n_eg, n_e = r64_run["grad_evals"], r64_run["energy_evals"]
+    # the dominant kernel over the step: k_pair64_sym in both of its forms,
+    # weighted by the step's own launch mix (n_eg E + grad, n_e energy only)
+    step_ms = n_eg * ms_pair + n_e * ms_pair_e
+    step_alg = (n_eg * FLOPS_UNIQUE_EG + n_e * FLOPS_UNIQUE_E) * unique / (step_ms / 1e3) / 1e12
+    step_hw = (n_eg * HW_SYM_EG + n_e * HW_SYM_E) * unique / (step_ms / 1e3) / 1e12
+    step32_ms = ms_pair32 + 3 * ms_pair32_d  # a MIXED L-BFGS step: one E + grad, three trials
+    step32_alg = (FLOPS_UNIQUE_EG + 3 * FLOPS_UNIQUE_E) * unique / (step32_ms / 1e3) / 1e12
     line = {
         "metric": METRIC,
         "value": value,
@@ -322,15 +336,19 @@ def bench_gpu(args):
                 "h2d_bytes_per_step": 8 * 3 * N_ATOMS, "d2h_bytes_per_step": 8 * 3 * N_ATOMS},
         "gpu_launches": int(launches),
         "clocks": clocks,
-        "roofline": {"bound": "alu", "achieved": r64["achieved"], "peak": fp64_derived, "unit": "TFLOP/s",
-                     "frac": r64["frac"], "traffic": profiled_traffic("k_pair<double,128,1> E+grad"),
-                     "kernel": "k_pair<double,128,1> E+grad",
-                     "work": f"{FLOPS_UNIQUE_EG:.0f} flops x N(N-1)/2 unique pairs per launch (algorithmic)",
-                     "ms_per_launch": ms_pair,
-                     "hw_achieved": r64["hw_achieved"], "hw_frac": r64["hw_frac"],
-                     "hw_work": f"{FLOPS_PER_PAIR_EG:.0f} flops x N(N-1) evaluated pairs (row sweep)",
+        "roofline": {"bound": "alu", "achieved": step_alg, "peak": fp64_derived, "unit": "TFLOP/s",
+                     "frac": step_alg / fp64_derived, "traffic": profiled_traffic("k_pair64_sym E+grad"),
+                     "kernel": "k_pair64_sym (E+grad and E-only launches in the step's mix)",
+                     "work": f"{FLOPS_UNIQUE_EG:.0f} (E+grad) / {FLOPS_UNIQUE_E:.0f} (E) flops x N(N-1)/2 "
+                             f"unique pairs per launch (algorithmic); {n_eg} + {n_e} launches per step",
+                     "ms_per_launch": step_ms / (n_eg + n_e),
+                     "hw_achieved": step_hw, "hw_frac": step_hw / fp64_derived,
+                     "hw_work": f"{HW_SYM_EG:.0f} / {HW_SYM_E:.0f} flops per unique pair as executed "
+                                "(each pair once, force added to both atoms)",
                      "peak_source": f"derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x {sm_max_mhz:.0f} MHz",
-                     "peak_probe": fp64_probe, "frac_of_probe": r64["achieved"] / fp64_probe,
+                     "peak_probe": fp64_probe, "frac_of_probe": step_alg / fp64_probe,
+                     "e_grad": {"ms_per_launch": ms_pair, "achieved": r64["achieved"], "frac": r64["frac"],
+                                "hw_frac": r64["hw_frac"]},
                      "e_only": {"ms_per_launch": ms_pair_e, "achieved": r64e["achieved"], "frac": r64e["frac"],
                                 "hw_frac": r64e["hw_frac"]}},
         "mixed": {"value": value32, "unit": "pair interactions/s (E and E+grad evaluations)",
@@ -338,13 +356,15 @@ def bench_gpu(args):
                   "autotuned_items_per_block": density32,
                   "vs_plain_gpu": value32 / value,
                   "error_vs_fp64_at_start": mixed_err,
-                  "roofline": {"bound": "alu", "kernel": "k_pair<float,64,2> E+grad",
-                               "achieved": r32["achieved"], "peak": fp32_derived, "unit": "TFLOP/s",
-                               "frac": r32["frac"], "hw_achieved": r32["hw_achieved"], "hw_frac": r32["hw_frac"],
-                               "ms_per_launch": ms_pair32,
+                  "roofline": {"bound": "alu", "kernel": "k_pair<float,64,2> (a MIXED L-BFGS step's mix: "
+                                                            "one E+grad row sweep, three difference trials)",
+                               "achieved": step32_alg, "peak": fp32_derived, "unit": "TFLOP/s",
+                               "frac": step32_alg / fp32_derived,
+                               "e_grad": {"ms_per_launch": ms_pair32, "frac": r32["frac"],
+                                          "hw_frac": r32["hw_frac"]},
                                "traffic": profiled_traffic("k_pair<float,64,2> E+grad"),
                                "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 flops x {sm_max_mhz:.0f} MHz",
-                               "peak_probe": fp32_probe, "frac_of_probe": r32["achieved"] / fp32_probe,
+                               "peak_probe": fp32_probe, "frac_of_probe": step32_alg / fp32_probe,
                                "e_only": {"ms_per_launch": ms_pair32_e, "frac": r32e["frac"],
                                           "hw_frac": r32e["hw_frac"]},
                                "difference_trial": {"ms_per_launch": ms_pair32_d, "frac": r32d["frac"],
@@ -462,6 +482,7 @@ def methods_3334(ffmin, torch, dev, s3, cap=3000, gradfree_sweeps=10):
         if prec == ffmin.FFMIN_FP64:
             res["start_energy"] = S.energy_grad(x0.clone())[0][0]
         runs = [(m, m, {}) for m in ("GD", "FGM", "CG", "LBFGS", "OGM", "GRADFREE")]
+        runs.insert(2, ("FGM_RESTART", "FGM", dict(fgm_restart=1)))
         runs.append(("GRADFREE_EPOCHS64", "GRADFREE", dict(gradfree_parts=64, gradfree_margin=1.0)))
         for name, method, extra in runs:
             cap_m = gradfree_sweeps * s3.n_atoms if method == "GRADFREE" else cap
@@ -598,8 +619,9 @@ def bench_reference(args):
 
 
 def profile_run(args):
-    """Small fixed workloads for ncu captures.  Default: one E + grad E of
-    the 30,000-atom globule with the MIXED pair kernel, then one with FP64.
+    """Small fixed workloads for ncu captures.  Default: E + grad E and E of
+    the 30,000-atom globule in FP64, then E + grad E, E and one difference
+    trial in MIXED.
     --profile-minimize K: a K-step MIXED L-BFGS run of the 3,334-atom globule
     (every kernel of the minimizer pipeline).  --profile-batch K: K steps of
     the 256-system batch.  --profile-vectors K: K FP64 L-BFGS steps of 1,024
@@ -675,13 +697,20 @@ def profile_run(args):
               "ms/tick", ev0.elapsed_time(ev1) / st["ticks"])
         S.close()
         return
+    # FP64 first (k_pair64_sym: E + grad, then E only), then MIXED (k_pair:
+    # E + grad, E only, then a difference trial, i.e. the E + grad of its base
+    # and the trial itself); the MIXED object's FP64 kernel launches are empty
     s = synth.make_system(args.profile_atoms, SEED)
     x = torch.tensor(s.x.reshape(-1), dtype=torch.float64, device="cuda")
-    for prec in (ffmin.FFMIN_MIXED, ffmin.FFMIN_FP64):
+    r = -torch.ones_like(x) / math.sqrt(x.numel())
+    for prec in (ffmin.FFMIN_FP64, ffmin.FFMIN_MIXED):
         S = ffmin.System([s], prec)
         e, g = S.energy_grad(x)
+        e1 = S.energy(x)
+        if prec == ffmin.FFMIN_MIXED:
+            S.energy_delta(x, r, 0.01)
         torch.cuda.synchronize()
-        print("profile", prec, e[0])
+        print("profile", prec, e[0], e1[0])
         S.close()
 
 

@@ -55,9 +55,12 @@ typedef enum {
  * (Section 3); OGM: the optimized gradient method of Section 4 (Eq. 11) with
  * the step 1/L replaced by a line search from y (LS_PAR with G0 by default),
  * the gradient evaluated at y and at every x^k, t_0 = 1, no momentum restart
- * except after a failed line search. */
+ * except after a failed line search; HB: the heavy-ball method of Section 4
+ * (Eq. 8) with constant step options.hb_alpha and momentum options.hb_beta,
+ * x^{-1} = x^0, no line search (one E + grad per step). */
 typedef enum {
-    FFMIN_GD = 0, FFMIN_FGM = 1, FFMIN_CG = 2, FFMIN_LBFGS = 3, FFMIN_GRADFREE = 4, FFMIN_OGM = 5
+    FFMIN_GD = 0, FFMIN_FGM = 1, FFMIN_CG = 2, FFMIN_LBFGS = 3, FFMIN_GRADFREE = 4, FFMIN_OGM = 5,
+    FFMIN_HB = 6
 } ffmin_method;
 
 /* beta of CG (Section 5.1; Andrei 2008): d = previous unnormalised
@@ -149,6 +152,15 @@ typedef struct {
      * momentum dropped whenever f(x^{k+1}) > f(x^k)), which Algorithm 1 does
      * not have. */
     int32_t fgm_restart;
+    /* HB (Eq. 8): x^{k+1} = x^k - hb_alpha grad f(x^k) + hb_beta (x^k - x^{k-1});
+     * hb_alpha > 0 (A^2 mol/kcal), hb_beta >= 0; defaults 1e-4 and 0.5.  A
+     * non-finite evaluation stops the run at the last finite iterate. */
+    double hb_alpha, hb_beta;
+    /* GRADFREE: r_far > 0 replaces the Coulomb term of every atom at least
+     * r_far A from the moving atom's current position by its first-order
+     * Taylor expansion about that position (Section 3's linearised far
+     * field; Lennard-Jones stays exact); 0 (default): exact rows. */
+    double gradfree_taylor_r;
 } ffmin_options;
 
 typedef struct {

@@ -28,7 +28,7 @@ struct ParabState;
 cudaError_t launch_parab_move(const Ctx &c, ParabState *ps, int grid, cudaStream_t s);
 size_t parab_state_bytes();
 void parab_state_init(void *host_buf, int n, int atom0, int mode, int max_moves, uint64_t seed,
-                      double delta);
+                      double delta, double taylor_r);
 size_t parab_offset_move();
 size_t parab_offset_stop();
 cudaError_t launch_epoch(const Ctx &c, const EpochArgs &a, int parts, cudaStream_t s);
@@ -281,6 +281,9 @@ void ffmin_options_default(ffmin_options *o) {
     o->record_every = 0;
     o->record_slots = 0;
     o->fgm_restart = 0;
+    o->hb_alpha = 1e-4;
+    o->hb_beta = 0.5;
+    o->gradfree_taylor_r = 0.0;
 }
 
 const char *ffmin_status_string(ffmin_status s) {
@@ -861,7 +864,10 @@ ffmin_status ffmin_energy_delta(ffmin_system *sys, const double *x_dev, const do
 
 static ffmin_status check_options(ffmin_system *sys, const ffmin_options *o) {
     if (!o) return fail(sys, FFMIN_ERR_INVALID_ARG, "options is NULL");
-    if (o->method < FFMIN_GD || o->method > FFMIN_OGM) return fail(sys, FFMIN_ERR_INVALID_ARG, "bad method");
+    if (o->method < FFMIN_GD || o->method > FFMIN_HB) return fail(sys, FFMIN_ERR_INVALID_ARG, "bad method");
+    if (o->method == FFMIN_HB && !(o->hb_alpha > 0.0 && std::isfinite(o->hb_alpha) && o->hb_beta >= 0.0 &&
+                                   std::isfinite(o->hb_beta)))
+        return fail(sys, FFMIN_ERR_INVALID_ARG, "HB needs hb_alpha > 0 and hb_beta >= 0, both finite");
     if (o->cg_variant < 0 || o->cg_variant > FFMIN_CG_DY) return fail(sys, FFMIN_ERR_INVALID_ARG, "bad cg_variant");
     if (o->ls < 0 || o->ls > FFMIN_LS_PAR) return fail(sys, FFMIN_ERR_INVALID_ARG, "bad line search");
     if (o->method == FFMIN_LBFGS && (o->lbfgs_m < 1 || o->lbfgs_m > MAXM))
@@ -870,6 +876,8 @@ static ffmin_status check_options(ffmin_system *sys, const ffmin_options *o) {
         !(o->eps_h > 0.0 && o->eps_h < 1.0) || o->ls_par_K < 2 || !(o->gtol_inf >= 0.0) || o->max_iter < 0 ||
         o->max_evals < 1)
         return fail(sys, FFMIN_ERR_INVALID_ARG, "line-search / stopping parameter out of range");
+    if (o->method == FFMIN_GRADFREE && !(o->gradfree_taylor_r >= 0.0))
+        return fail(sys, FFMIN_ERR_INVALID_ARG, "gradfree_taylor_r must be >= 0");
     if (o->method == FFMIN_GRADFREE && (o->gradfree_parts < 0 || !(o->gradfree_margin >= 0.0)))
         return fail(sys, FFMIN_ERR_INVALID_ARG, "GRADFREE needs gradfree_parts >= 0 and gradfree_margin >= 0");
     if (o->method == FFMIN_GRADFREE && (sys->n_sys != 1 || !(o->gradfree_delta > 0.0)))
@@ -917,6 +925,8 @@ static ffmin_status minimize_dev(ffmin_system *sys, double *x_dev, const ffmin_o
         S.kminus = o->k_minus;
         S.eps_h = o->eps_h;
         S.fgm_restart = o->fgm_restart;
+        S.hb_alpha = o->hb_alpha;
+        S.hb_beta = o->hb_beta;
         S.precond_on = (o->use_learned_precond && o->method == FFMIN_LBFGS) ? 1 : 0;
         S.rec_ptr = o->record_dev;
         S.rec_every = o->record_dev ? o->record_every : 0;
@@ -1143,7 +1153,8 @@ static ffmin_status parab_minimize(ffmin_system *sys, const ffmin_options *o, ff
         sys->parab_grid = std::max(1, std::min((n + TI - 1) / TI, 2 * sms));
     }
     std::vector<char> hbuf(parab_state_bytes());
-    parab_state_init(hbuf.data(), n, (int)sys->atom_off[0], mode, o->max_iter, o->seed, o->gradfree_delta);
+    parab_state_init(hbuf.data(), n, (int)sys->atom_off[0], mode, o->max_iter, o->seed, o->gradfree_delta,
+                     o->gradfree_taylor_r);
     CK(cudaMemcpyAsync(sys->parab_state, hbuf.data(), hbuf.size(), cudaMemcpyHostToDevice, sys->stream));
     ffm::ParabState *ps = (ffm::ParabState *)sys->parab_state;
     if (!sys->parab_graph) {
@@ -1357,7 +1368,8 @@ static ffmin_status epoch_minimize(ffmin_system *sys, const ffmin_options *o, ff
         CK(cudaMemcpyAsync(sys->ep_ints, ints.data(), sizeof(int32_t) * ints.size(), cudaMemcpyHostToDevice,
                            sys->stream));
         EpochArgs ea{sys->ep_view, sys->ep_viewf, d_list, d_loff, d_allowed, d_members, d_moff,
-                     n, mode, o->seed, e, o->gradfree_delta};
+                     n, mode, o->seed, e, o->gradfree_delta,
+                     o->gradfree_taylor_r > 0.0 ? o->gradfree_taylor_r * o->gradfree_taylor_r : 0.0};
         CK(launch_epoch(c, ea, P, sys->stream));
         launches += 1;
         ticks += 1;

@@ -403,6 +403,19 @@ __device__ void ogm_step(SysState &S, int accept, int restart, double wds) {
     S.phase = PH_OGM_UPD;
 }
 
+// heavy ball (Section 4, Eq. 8): the update kernel accepts the evaluated
+// iterate (accept = 1) or starts with x^{-1} = x^0 (accept = 0), then forms
+// the next iterate in XT, which the same round's pair kernel evaluates
+__device__ void hb_step(SysState &S, int accept) {
+    S.upd.op = U_HB;
+    S.upd.accept = accept;
+    S.upd.restart = !accept;
+    S.upd.a = S.hb_alpha;
+    S.upd.b = S.hb_beta;
+    set_eval(S, EV_EG, V_XT, -1, 0.0, 1.0);
+    S.phase = PH_HB;
+}
+
 // reductions of the finalize kernel
 enum { RF_E = 0, RF_GG, RF_GINF, RF_GTG, RF_GTR, RF_BAD, RF_EPAIR, RF_N };
 
@@ -460,6 +473,14 @@ __device__ void on_eval_done(const Ctx &c, SysState &S, const double *v) {
             finish(c, S, FFMIN_OK, S.f, S.ginf);
             return;
         }
+        if (S.method == FFMIN_HB) {
+            if (cap_hit(S)) {
+                finish(c, S, FFMIN_ERR_MAX_ITER, S.f, S.ginf);
+                return;
+            }
+            hb_step(S, 0);
+            return;
+        }
         if (S.method == FFMIN_OGM) {  // x^0 = X, t_0 = 1, DS = grad f(x^0)
             if (cap_hit(S)) {
                 finish(c, S, FFMIN_ERR_MAX_ITER, S.f, S.ginf);
@@ -471,6 +492,24 @@ __device__ void on_eval_done(const Ctx &c, SysState &S, const double *v) {
         }
         set_dir(S, 1, -1.0, 0.0, 1.0, 1);
         S.phase = PH_DIR;
+        return;
+    }
+
+    if (S.phase == PH_HB) {  // x^{k+1} evaluated: accept it (no line search)
+        if (bad) {  // the run ends at the last finite iterate, still in X
+            finish(c, S, FFMIN_ERR_NONFINITE, S.f, S.ginf);
+            return;
+        }
+        S.iter++;
+        S.f = E;
+        S.ginf = v[RF_GINF];
+        S.gg = v[RF_GG];
+        hb_step(S, 1);
+        if (S.ginf < S.gtol || mixed_handover(S, E, S.ginf)) {
+            finish(c, S, FFMIN_OK, S.f, S.ginf);
+            return;
+        }
+        if (cap_hit(S)) finish(c, S, FFMIN_ERR_MAX_ITER, S.f, S.ginf);
         return;
     }
 

@@ -44,13 +44,15 @@ enum UpdKind : int {
     U_FGM_ACCEPT,    // Xn = fma(h, R * inv, W); P <- Xn - X (0 on restart); X <- Xn (XB <- Xn)
     U_FGM_RESET,     // X <- W, P <- 0
     U_FGM_BEST_W,    // XB <- W
-    U_OGM            // OGM: (accept) X <- XT, G <- GT; (restart) X0 <- X, DS <- G, else
+    U_OGM,           // OGM: (accept) X <- XT, G <- GT; (restart) X0 <- X, DS <- G, else
                      // (accept) DS += h G; then W = a X + b X0, R = -(a G + inv DS), <R, R>
+    U_HB             // heavy ball: (accept) P <- X, X <- XT, G <- GT; (start) P <- X;
+                     // then XT = fma(b, X - P, fma(-a, G, X)), the next iterate
 };
 
 enum Phase : int {
     PH_IDLE = 0, PH_START, PH_DIR, PH_LS, PH_ACCEPT, PH_FGM_W, PH_FINAL, PH_EVAL_ONLY, PH_DONE,
-    PH_OGM_UPD, PH_OGM_Y
+    PH_OGM_UPD, PH_OGM_Y, PH_HB
 };
 
 // a pair item (i-tile, j-chunk); tile < 0 marks a bonded item whose j0, nj
@@ -117,6 +119,7 @@ struct SysState {
     double ogm_t;  // OGM: t_k
     int32_t xb_known, result_slot;
     int32_t fgm_restart, fgm_pad;  // 1: function-value momentum restart (not in Algorithm 1)
+    double hb_alpha, hb_beta;      // heavy ball (Eq. 8): constant step and momentum
     // result
     double res_f, res_ginf;
     // learned preconditioner in use for this run
@@ -227,6 +230,7 @@ struct EpochArgs {
     int n, mode;
     uint64_t seed, epoch;
     double delta;
+    double taylor_r2;       // squared far-field radius of the linearised Coulomb rows, 0 = exact
 };
 
 }  // namespace ffm

@@ -5,6 +5,12 @@
 // 8th point) and moves the atom to the best of the 8 (ties: the earlier
 // point).  |grad E|_inf is checked after every sweep of N moves.
 //
+// With a far-field radius r_far > 0 (options.gradfree_taylor_r), the Coulomb
+// term of every atom j at least r_far from atom i's current position x_i is
+// replaced by its first-order Taylor expansion about x_i, e0 (1 + d0.(p -
+// x_i) / r0^2) with d0 = x_j - x_i and e0 its value at x_i (Section 3's
+// linearised far field for single-atom moves); Lennard-Jones stays exact.
+//
 // The random atom of move k is the k-th output of the counter-based
 // SplitMix64 stream (Steele, Lea and Flood 2014) with the user's seed, scaled
 // to [0, N) by a 64x64 -> 128-bit multiply (high word).
@@ -29,6 +35,7 @@ struct ParabState {
     int32_t atom0, mode, atom, best;
     uint64_t seed;
     double delta;
+    double taylor_r2;  // r_far^2 of the linearised far field, 0 = exact rows
     double f[8];
     double p[8][3];
 };
@@ -44,55 +51,102 @@ __device__ __forceinline__ int pick_atom(uint64_t seed, uint64_t k, int n) {
     return (int)__umul64hi(splitmix64(seed, k), (uint64_t)n);
 }
 
-// pair part of the row energy of atom i placed at each of NP positions,
-// this thread's share of the j atoms (FP64 accumulation; pair terms in the
-// system's precision mode)
+// Pair part of the row energy of atom i placed at each of NP positions,
+// this thread's share of the j atoms: j = j0, j0 + stride, ... (FP64
+// accumulation of FP64 terms, or FP32 sums of FP32 terms in the mixed form);
+// pos / posf give the other atoms, xi atom i's current position, tr2 the
+// squared far-field radius (0: exact rows).
 template <int NP>
-__device__ void row_partial(const Ctx &c, int mode, int atom0, int n, int i, const double (*p)[3],
-                            double *acc) {
+__device__ void row_sums(const Ctx &c, int mode, const double4_32a *pos, const float4 *posf,
+                         const double2 *par, const float2 *parf, int n, int i, const double (*p)[3],
+                         const double *xi, double tr2, int j0, int stride, double *acc) {
     for (int q = 0; q < NP; q++) acc[q] = 0.0;
-    const int stride = gridDim.x * blockDim.x;
     if (mode == 1) {
-        const double qi = c.posd[atom0 + i].w;
-        const double2 ci = c.pard[atom0 + i];
-        for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+        const double qi = pos[i].w;
+        const double2 ci = par[i];
+        for (int j = j0; j < n; j += stride) {
             if (j == i) continue;
-            const double4_32a pj = c.posd[atom0 + j];
-            const double2 cj = c.pard[atom0 + j];
+            const double4_32a pj = pos[j];
+            const double2 cj = par[j];
             const double c6 = ci.x * cj.x, c12 = ci.y * cj.y, qq = qi * pj.w;
+            bool far = false;
+            double e0 = 0.0, fac = 0.0;
+            const double d0x = pj.x - xi[0], d0y = pj.y - xi[1], d0z = pj.z - xi[2];
+            if (tr2 > 0.0) {
+                const double r02 = d0x * d0x + d0y * d0y + d0z * d0z;
+                if (r02 >= tr2) {
+                    far = true;
+                    e0 = qq * rsqrt(r02);
+                    fac = e0 / r02;
+                }
+            }
             for (int q = 0; q < NP; q++) {
                 const double dx = pj.x - p[q][0], dy = pj.y - p[q][1], dz = pj.z - p[q][2];
                 const double r2 = dx * dx + dy * dy + dz * dz;
                 const double ri = rsqrt(r2);
                 const double ri2 = ri * ri, ri6 = ri2 * ri2 * ri2;
-                acc[q] += qq * ri + ri6 * (c12 * ri6 - c6) * (1.0 / 6.0);
+                const double lj = ri6 * (c12 * ri6 - c6) * (1.0 / 6.0);
+                if (far) {
+                    const double dd = d0x * (p[q][0] - xi[0]) + d0y * (p[q][1] - xi[1]) + d0z * (p[q][2] - xi[2]);
+                    acc[q] += e0 + fac * dd + lj;
+                } else {
+                    acc[q] += qq * ri + lj;
+                }
             }
         }
     } else {
-        const float qi = c.posf[atom0 + i].w;
-        const float2 ci = c.parf[atom0 + i];
+        const float qi = posf[i].w;
+        const float2 ci = parf[i];
         float pf[NP][3], accf[NP];
         for (int q = 0; q < NP; q++) {
             accf[q] = 0.f;
             for (int a = 0; a < 3; a++) pf[q][a] = (float)p[q][a];
         }
+        const float xf[3] = {(float)xi[0], (float)xi[1], (float)xi[2]};
+        const float tr2f = (float)tr2;
         // FP32 sums of this thread's j (tile-local FP32 accumulation of the
         // mixed form), FP64 from the block reduction on
-        for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+        for (int j = j0; j < n; j += stride) {
             if (j == i) continue;
-            const float4 pj = c.posf[atom0 + j];
-            const float2 cj = c.parf[atom0 + j];
+            const float4 pj = posf[j];
+            const float2 cj = parf[j];
             const float c6 = ci.x * cj.x, c12 = ci.y * cj.y, qq = qi * pj.w;
+            bool far = false;
+            float e0 = 0.f, fac = 0.f;
+            const float d0x = pj.x - xf[0], d0y = pj.y - xf[1], d0z = pj.z - xf[2];
+            if (tr2f > 0.f) {
+                const float r02 = d0x * d0x + d0y * d0y + d0z * d0z;
+                if (r02 >= tr2f) {
+                    far = true;
+                    e0 = qq * rsqrtf(r02);
+                    fac = e0 / r02;
+                }
+            }
             for (int q = 0; q < NP; q++) {
                 const float dx = pj.x - pf[q][0], dy = pj.y - pf[q][1], dz = pj.z - pf[q][2];
                 const float r2 = dx * dx + dy * dy + dz * dz;
                 const float ri = rsqrtf(r2);
                 const float ri2 = ri * ri, ri6 = ri2 * ri2 * ri2;
-                accf[q] += qq * ri + ri6 * (c12 * ri6 - c6) * (1.0f / 6.0f);
+                const float lj = ri6 * (c12 * ri6 - c6) * (1.0f / 6.0f);
+                if (far) {
+                    const float dd = d0x * (pf[q][0] - xf[0]) + d0y * (pf[q][1] - xf[1]) + d0z * (pf[q][2] - xf[2]);
+                    accf[q] += e0 + fac * dd + lj;
+                } else {
+                    accf[q] += qq * ri + lj;
+                }
             }
         }
         for (int q = 0; q < NP; q++) acc[q] = (double)accf[q];
     }
+}
+
+// the grid's share of one row evaluation over the system's atoms
+template <int NP>
+__device__ void row_partial(const Ctx &c, const ParabState *ps, int i, const double (*p)[3], const double *xi,
+                            double *acc) {
+    const int a0 = ps->atom0;
+    row_sums<NP>(c, ps->mode, c.posd + a0, c.posf + a0, c.pard + a0, c.parf + a0, ps->n, i, p, xi, ps->taylor_r2,
+                 blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, acc);
 }
 
 // bonded terms containing atom i (global index a) with atom i at p
@@ -120,7 +174,7 @@ __global__ void __launch_bounds__(TI) k_parab_rows(Ctx c, ParabState *ps) {
         p[2 + 2 * a][a] = p[2 + 2 * a][a] - ps->delta;
     }
     double acc[7];
-    row_partial<7>(c, ps->mode, atom0, n, i, p, acc);
+    row_partial<7>(c, ps, i, p, p[0], acc);  // p[0]: the current position
     double v[7];
     for (int q = 0; q < 7; q++) v[q] = acc[q];
     block_reduce_store<7>(v, 0u, &c.red[(int64_t)blockIdx.x * NRED]);
@@ -152,11 +206,11 @@ __global__ void __launch_bounds__(TI) k_parab_rows(Ctx c, ParabState *ps) {
 // the vertex row, the decision and the move
 __global__ void __launch_bounds__(TI) k_parab_vertex(Ctx c, ParabState *ps) {
     if (ps->move >= ps->stop_at) return;
-    const int n = ps->n, atom0 = ps->atom0, i = ps->atom;
+    const int atom0 = ps->atom0, i = ps->atom;
     double p[1][3];
     for (int a = 0; a < 3; a++) p[0][a] = ps->p[7][a];
     double acc[1];
-    row_partial<1>(c, ps->mode, atom0, n, i, p, acc);
+    row_partial<1>(c, ps, i, p, ps->p[0], acc);  // ps->p[0]: the current position
     double v[1] = {acc[0]};
     block_reduce_store<1>(v, 0u, &c.red[(int64_t)blockIdx.x * NRED]);
     if (!last_block(&c.counters[CNT_PARAB2])) return;
@@ -193,7 +247,7 @@ cudaError_t launch_parab_move(const Ctx &c, ParabState *ps, int grid, cudaStream
 size_t parab_state_bytes() { return sizeof(ParabState); }
 
 void parab_state_init(void *host_buf, int n, int atom0, int mode, int max_moves, uint64_t seed,
-                      double delta) {
+                      double delta, double taylor_r) {
     ParabState ps;
     std::memset(&ps, 0, sizeof(ps));
     ps.n = n;
@@ -203,6 +257,7 @@ void parab_state_init(void *host_buf, int n, int atom0, int mode, int max_moves,
     ps.stop_at = 0;
     ps.seed = seed;
     ps.delta = delta;
+    ps.taylor_r2 = taylor_r > 0.0 ? taylor_r * taylor_r : 0.0;
     std::memcpy(host_buf, &ps, sizeof(ps));
 }
 
@@ -222,10 +277,13 @@ size_t parab_offset_stop() { return offsetof(ParabState, stop_at); }
 constexpr int EPOCH_THREADS = 256;
 
 // row sums of NP positions of atom i over the part's copy: this thread's j
+// (the part's FP64 copy V is read through a double4-free view: positions
+// from V, charges q' from c.qs)
 template <int NP>
 __device__ void epoch_rows(const Ctx &c, const EpochArgs &a, const double *V, const float4 *Vf, int i,
                            const double (*p)[3], double *acc) {
     for (int q = 0; q < NP; q++) acc[q] = 0.0;
+    const double xi[3] = {V[3 * i], V[3 * i + 1], V[3 * i + 2]};  // current position
     if (a.mode == 1) {
         const double qi = c.qs[i];
         const double2 ci = c.pard[i];
@@ -234,36 +292,33 @@ __device__ void epoch_rows(const Ctx &c, const EpochArgs &a, const double *V, co
             const double xj = V[3 * j], yj = V[3 * j + 1], zj = V[3 * j + 2];
             const double2 cj = c.pard[j];
             const double c6 = ci.x * cj.x, c12 = ci.y * cj.y, qq = qi * c.qs[j];
+            bool far = false;
+            double e0 = 0.0, fac = 0.0;
+            const double d0x = xj - xi[0], d0y = yj - xi[1], d0z = zj - xi[2];
+            if (a.taylor_r2 > 0.0) {
+                const double r02 = d0x * d0x + d0y * d0y + d0z * d0z;
+                if (r02 >= a.taylor_r2) {
+                    far = true;
+                    e0 = qq * rsqrt(r02);
+                    fac = e0 / r02;
+                }
+            }
             for (int q = 0; q < NP; q++) {
                 const double dx = xj - p[q][0], dy = yj - p[q][1], dz = zj - p[q][2];
                 const double r2 = dx * dx + dy * dy + dz * dz;
                 const double ri = rsqrt(r2);
                 const double ri2 = ri * ri, ri6 = ri2 * ri2 * ri2;
-                acc[q] += qq * ri + ri6 * (c12 * ri6 - c6) * (1.0 / 6.0);
+                const double lj = ri6 * (c12 * ri6 - c6) * (1.0 / 6.0);
+                if (far) {
+                    const double dd = d0x * (p[q][0] - xi[0]) + d0y * (p[q][1] - xi[1]) + d0z * (p[q][2] - xi[2]);
+                    acc[q] += e0 + fac * dd + lj;
+                } else {
+                    acc[q] += qq * ri + lj;
+                }
             }
         }
-    } else {
-        const float qi = Vf[i].w;
-        const float2 ci = c.parf[i];
-        float pf[NP][3], accf[NP];
-        for (int q = 0; q < NP; q++) {
-            accf[q] = 0.f;
-            for (int k = 0; k < 3; k++) pf[q][k] = (float)p[q][k];
-        }
-        for (int j = threadIdx.x; j < a.n; j += blockDim.x) {  // FP32 sums of this thread's j
-            if (j == i) continue;
-            const float4 pj = Vf[j];
-            const float2 cj = c.parf[j];
-            const float c6 = ci.x * cj.x, c12 = ci.y * cj.y, qq = qi * pj.w;
-            for (int q = 0; q < NP; q++) {
-                const float dx = pj.x - pf[q][0], dy = pj.y - pf[q][1], dz = pj.z - pf[q][2];
-                const float r2 = dx * dx + dy * dy + dz * dz;
-                const float ri = rsqrtf(r2);
-                const float ri2 = ri * ri, ri6 = ri2 * ri2 * ri2;
-                accf[q] += qq * ri + ri6 * (c12 * ri6 - c6) * (1.0f / 6.0f);
-            }
-        }
-        for (int q = 0; q < NP; q++) acc[q] = (double)accf[q];
+    } else {  // FP32 sums of this thread's j
+        row_sums<NP>(c, 0, nullptr, Vf, nullptr, c.parf, a.n, i, p, xi, a.taylor_r2, threadIdx.x, blockDim.x, acc);
     }
 }
 

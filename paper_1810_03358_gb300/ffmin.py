@@ -19,13 +19,13 @@ FFMIN_OK, FFMIN_ERR_INVALID_ARG, FFMIN_ERR_CUDA, FFMIN_ERR_NONFINITE = 0, 1, 2, 
 FFMIN_ERR_LINESEARCH, FFMIN_ERR_MAX_ITER, FFMIN_ERR_TIMEOUT, FFMIN_ERR_OOM = 4, 5, 6, 7
 STATUS_NAMES = {0: "ok", 1: "invalid_arg", 2: "cuda", 3: "nonfinite", 4: "linesearch",
                 5: "max_iter", 6: "timeout", 7: "oom"}
-FFMIN_GD, FFMIN_FGM, FFMIN_CG, FFMIN_LBFGS, FFMIN_GRADFREE, FFMIN_OGM = range(6)
+FFMIN_GD, FFMIN_FGM, FFMIN_CG, FFMIN_LBFGS, FFMIN_GRADFREE, FFMIN_OGM, FFMIN_HB = range(7)
 (FFMIN_CG_PRP, FFMIN_CG_HS, FFMIN_CG_FR, FFMIN_CG_PRP_PLUS, FFMIN_CG_CD, FFMIN_CG_LS,
  FFMIN_CG_DY) = range(7)
 FFMIN_LS_DEFAULT, FFMIN_LS_H, FFMIN_LS_PAR = range(3)
 FFMIN_FP64, FFMIN_MIXED = 0, 1
 METHODS = {"GD": FFMIN_GD, "FGM": FFMIN_FGM, "CG": FFMIN_CG, "LBFGS": FFMIN_LBFGS,
-           "GRADFREE": FFMIN_GRADFREE, "OGM": FFMIN_OGM}
+           "GRADFREE": FFMIN_GRADFREE, "OGM": FFMIN_OGM, "HB": FFMIN_HB}
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int32)
@@ -50,7 +50,8 @@ class ffmin_options(C.Structure):
                 ("gradfree_margin", C.c_double),
                 ("use_learned_precond", C.c_int32), ("max_ticks", C.c_int32),
                 ("record_dev", C.c_void_p), ("record_every", C.c_int32), ("record_slots", C.c_int32),
-                ("fgm_restart", C.c_int32)]
+                ("fgm_restart", C.c_int32), ("hb_alpha", C.c_double), ("hb_beta", C.c_double),
+                ("gradfree_taylor_r", C.c_double)]
 
 
 class ffmin_result(C.Structure):

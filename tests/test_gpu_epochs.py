@@ -96,3 +96,16 @@ def test_invalid_epoch_options(ff):
     with pytest.raises(ff.FfminError):
         S.minimize(x, method=4, gradfree_parts=2, gradfree_margin=-1.0)
     S.close()
+
+
+def test_epochs_with_taylor_far_field(ff, oracle_mod):
+    # parallel epochs with the linearised far-field Coulomb rows (8 parts,
+    # r_far = 7 A): the oracle's decisions move for move
+    s = synth.make_system(400, 860)
+    kw = dict(method=4, max_iter=1000, gtol_inf=1e-9, seed=31, gradfree_delta=0.05, gradfree_parts=8,
+              gradfree_margin=0.5, gradfree_taylor_r=7.0)
+    xg, rg, _ = run(ff, s, 0, **kw)
+    xo, ro = oracle_mod.minimize(s, s.x, **kw)
+    for k in ("iterations", "energy_evals", "grad_evals"):
+        assert rg[k] == ro[k], (k, rg, ro)
+    assert np.abs(xg - xo).max() < 1e-8

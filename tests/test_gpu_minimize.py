@@ -269,6 +269,42 @@ def test_ogm_long_capped_run(ff, oracle_mod, prec):
         assert abs(e1 - r["energy"]) <= 1e-5 * terms["sum_abs"], (e1, r)
 
 
+@pytest.mark.parametrize("beta", [0.0, 0.5, 0.9])
+def test_heavy_ball_prefix(ff, oracle_mod, beta):
+    # the heavy-ball method of Section 4 (Eq. 8, constant alpha and beta, no
+    # line search) from a partly relaxed start, where alpha = 1e-4 is inside
+    # the stable range: the same iterates as the oracle's
+    s = synth.make_system(80, 45)
+    s.x, _ = oracle_mod.minimize(s, s.x, method=3, max_iter=300)
+    kw = dict(method=6, hb_alpha=1e-4, hb_beta=beta, max_iter=PREFIX)
+    xg, rg, _ = run_gpu(ff, [s], 0, **kw)
+    prefix_parity(oracle_mod, s, xg[0], rg[0], kw)
+
+
+def test_heavy_ball_batched_and_mixed(ff, oracle_mod):
+    # a batch of 9 systems (the per-system reduction path) against their own
+    # oracle runs; then a MIXED capped run lowers the energy and reports the
+    # energy of its returned point
+    systems = []
+    for k in range(9):
+        s = synth.make_system(30 + 11 * k, 340 + k)
+        s.x, _ = oracle_mod.minimize(s, s.x, method=3, max_iter=200)
+        systems.append(s)
+    kw = dict(method=6, hb_alpha=1e-4, hb_beta=0.6, max_iter=PREFIX)
+    xg, rg, _ = run_gpu(ff, systems, 0, **kw)
+    for b, s in enumerate(systems):
+        prefix_parity(oracle_mod, s, xg[b], rg[b], kw)
+    s = systems[-1]
+    xg, rg, _ = run_gpu(ff, [s], 1, method=6, hb_alpha=1e-4, hb_beta=0.6, max_iter=2000)
+    r = rg[0]
+    assert r["status_name"] in ("ok", "max_iter"), r
+    e0 = oracle_mod.energy(s, s.x)
+    e1 = oracle_mod.energy(s, xg[0])
+    assert e1 < e0
+    terms = oracle_mod.energy_terms(s, xg[0])[0]
+    assert abs(e1 - r["energy"]) <= 1e-5 * terms["sum_abs"], (e1, r)
+
+
 def test_evaluation_cap(ff, oracle_mod):
     s = synth.make_system(30, 29)
     kw = dict(method=3, max_evals=57)

@@ -62,3 +62,27 @@ def test_invalid_parameters(oracle_mod):
     A, b, _ = spd(4, 5.0, 13)
     _, r = oracle_mod.minimize_fn(quad_fg(A, b), np.zeros(4), method=oracle_mod.HB, hb_alpha=0.0)
     assert r["status_name"] == "bad_arg"
+
+
+def test_heavy_ball_stops_at_last_finite_iterate(oracle_mod):
+    # an objective that turns non-finite at its 6th gradient evaluation: the
+    # run stops there and returns the 5th iterate (the last finite one) with
+    # its energy, not the failing point
+    A = np.diag([1.0, 4.0, 9.0])
+    calls = {"n": 0}
+    iterates = []
+
+    def fg(x, want):
+        calls["n"] += 1
+        if calls["n"] >= 6:
+            return float("nan"), np.full(3, np.nan)
+        iterates.append(x.copy())
+        return 0.5 * x @ A @ x, A @ x
+
+    x0 = np.array([1.0, -2.0, 0.5])
+    xo, r = oracle_mod.minimize_fn(fg, x0, method=oracle_mod.HB, hb_alpha=0.05, hb_beta=0.3,
+                                   gtol_inf=1e-12, max_iter=100)
+    assert r["status_name"] == "nonfinite"
+    assert r["iterations"] == 4  # x^1 .. x^4 accepted; x^5 (6th call) failed
+    assert np.array_equal(xo, iterates[-1])
+    assert r["energy"] == 0.5 * iterates[-1] @ A @ iterates[-1]
