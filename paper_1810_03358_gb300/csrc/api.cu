@@ -15,9 +15,19 @@
 #include <map>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "ffmin_internal.cuh"
 
 using namespace ffm;
+
+// NVTX range over one entry point (visible to profilers; no cost otherwise)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // work-item densities (items per resident pair-kernel block) the autotuner tries
 static const int AUTOTUNE_DENSITIES[] = {3, 6, 10, 20};
@@ -784,6 +794,7 @@ static ffmin_status eval_all(ffmin_system *sys, const double *x_dev, int kind) {
 extern "C" {
 
 ffmin_status ffmin_energy(ffmin_system *sys, const double *x_dev, double *e_host) {
+    NvtxRange nvtx_range("ffmin_energy");
     ffmin_status st = enter(sys);
     if (st != FFMIN_OK) return st;
     if (!x_dev || !e_host) return fail(sys, FFMIN_ERR_INVALID_ARG, "NULL argument");
@@ -799,6 +810,7 @@ ffmin_status ffmin_energy(ffmin_system *sys, const double *x_dev, double *e_host
 }
 
 ffmin_status ffmin_energy_grad(ffmin_system *sys, const double *x_dev, double *e_host, double *g_dev) {
+    NvtxRange nvtx_range("ffmin_energy_grad");
     ffmin_status st = enter(sys);
     if (st != FFMIN_OK) return st;
     if (!x_dev || !e_host || !g_dev) return fail(sys, FFMIN_ERR_INVALID_ARG, "NULL argument");
@@ -839,6 +851,7 @@ ffmin_status ffmin_energy_grad_host(ffmin_system *sys, const double *x_host, dou
 
 ffmin_status ffmin_energy_delta(ffmin_system *sys, const double *x_dev, const double *r_dev, double h,
                                 double *de_host) {
+    NvtxRange nvtx_range("ffmin_energy_delta");
     ffmin_status st = enter(sys);
     if (st != FFMIN_OK) return st;
     if (!x_dev || !r_dev || !de_host || !std::isfinite(h)) return fail(sys, FFMIN_ERR_INVALID_ARG, "bad argument");
@@ -998,6 +1011,7 @@ static ffmin_status minimize_dev(ffmin_system *sys, double *x_dev, const ffmin_o
 }
 
 ffmin_status ffmin_minimize(ffmin_system *sys, double *x_dev, const ffmin_options *o, ffmin_result *res) {
+    NvtxRange nvtx_range("ffmin_minimize");
     ffmin_status st = enter(sys);
     if (st != FFMIN_OK) return st;
     if (!x_dev || !res) return fail(sys, FFMIN_ERR_INVALID_ARG, "NULL argument");
@@ -1008,6 +1022,7 @@ ffmin_status ffmin_minimize(ffmin_system *sys, double *x_dev, const ffmin_option
 }
 
 ffmin_status ffmin_minimize_host(ffmin_system *sys, double *x_host, const ffmin_options *o, ffmin_result *res) {
+    NvtxRange nvtx_range("ffmin_minimize_host");
     ffmin_status st = enter(sys);
     if (st != FFMIN_OK) return st;
     if (!x_host || !res) return fail(sys, FFMIN_ERR_INVALID_ARG, "NULL argument");
@@ -1070,6 +1085,7 @@ ffmin_status ffmin_neighbour_counts(ffmin_system *sys, const double *x_dev, int3
 }
 
 ffmin_status ffmin_autotune(ffmin_system *sys, const double *x_dev, int32_t *density_out) {
+    NvtxRange nvtx_range("ffmin_autotune");
     ffmin_status st = enter(sys);
     if (st != FFMIN_OK) return st;
     if (!x_dev) return fail(sys, FFMIN_ERR_INVALID_ARG, "NULL argument");
