@@ -97,10 +97,11 @@ typedef struct {
     /* 0: every pair interacts (Section 2).  1: a force-field variant, not in
      * the paper: pairs joined by a bond or by the ends of an angle are
      * excluded, the end atoms of a dihedral interact scaled by scale14
-     * (finite, >= 0).  Evaluated as FP64 correction terms (weight s - 1 on
-     * the pair term) beside the all-pairs sweep; FFMIN_FP64 only
-     * (ffmin_create rejects a MIXED batch with exclusions: the FP32 sweep's
-     * rounding of the excluded clashes would not cancel). */
+     * (finite, >= 0).  FP64 pair terms: FP64 correction terms (weight s - 1
+     * on the pair term) beside the all-pairs sweep.  FP32 pair terms (MIXED):
+     * the sweeps scale the listed pairs inside their sums (an FP32
+     * correction could not cancel the rounding of the excluded clashes); the
+     * MIXED gradient-free search refuses the variant. */
     int32_t exclusions;
     double scale14;
 } ffmin_topology;

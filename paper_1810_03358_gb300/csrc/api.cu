@@ -75,6 +75,8 @@ struct ffmin_system {
     int32_t *ep_ints = nullptr;  // list [N], members [N], loff, moff [P + 1], allowed [P]
     // learned preconditioner
     bool have_precond = false;
+    // some system uses the exclusion variant
+    bool has_excl = false;
     // stats of the last minimize
     int64_t last_ticks = 0, last_launches = 0, last_pairs = 0;
     // host copies of the topology needed by the gradient-free path
@@ -368,12 +370,11 @@ ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t pre
         if ((t.exclusions != 0 && t.exclusions != 1) ||
             (t.exclusions && !(t.scale14 >= 0.0 && std::isfinite(t.scale14))))
             return fail(nullptr, FFMIN_ERR_INVALID_ARG, "exclusions must be 0 or 1, scale14 finite and >= 0");
-        // the corrections cancel the excluded terms of the all-pairs sweep:
-        // exact in FP64, but the FP32 sweep's rounding of bonded-neighbour
-        // clashes (up to 1e10 kcal/mol at a jittered start) would swamp the
-        // energy, so exclusions run on the FP64 path only
-        if (t.exclusions && precision == FFMIN_MIXED)
-            return fail(nullptr, FFMIN_ERR_INVALID_ARG, "exclusions need precision FFMIN_FP64");
+        // FP64 terms: FP64 correction terms cancel the excluded terms of the
+        // all-pairs sweep; FP32 terms (MIXED): the sweeps scale the listed
+        // pairs inside their sums, since an FP32 correction could not cancel
+        // the rounding of bonded-neighbour clashes (up to 1e10 kcal/mol at a
+        // jittered start)
         total += t.n_atoms;
     }
     if (total > (1LL << 30)) return fail(nullptr, FFMIN_ERR_INVALID_ARG, "too many atoms");
@@ -414,6 +415,7 @@ ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t pre
     std::vector<double> xw;          // and weights s_ij - 1
     std::vector<int32_t> xcount(n_sys, 0);
     std::vector<std::vector<int2>> inc_lists(total);
+    std::vector<std::vector<std::pair<int32_t, float>>> xs_lists(total);  // scaled partners per atom
     for (int b = 0; b < n_sys; b++) {
         const ffmin_topology &t = tops[b];
         const int64_t A = sys->atom_off[b];
@@ -479,6 +481,8 @@ ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t pre
                 xw.push_back(w);
                 inc_lists[A + i].push_back(make_int2((3 << 2) | 0, term));
                 inc_lists[A + j].push_back(make_int2((3 << 2) | 1, term));
+                xs_lists[A + i].push_back(std::make_pair((int32_t)(A + j), (float)kv.second));
+                xs_lists[A + j].push_back(std::make_pair((int32_t)(A + i), (float)kv.second));
                 xcount[b]++;
             }
         }
@@ -489,6 +493,13 @@ ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t pre
             tl.sys = b;
             tl.a0 = (int)(A + a0);
             tl.na = std::min(TI, t.n_atoms - a0);
+            tl.xlo = std::numeric_limits<int32_t>::max();
+            tl.xhi = -1;
+            for (int a = tl.a0; a < tl.a0 + tl.na; a++)
+                for (const auto &pr : xs_lists[a]) {
+                    tl.xlo = std::min(tl.xlo, pr.first);
+                    tl.xhi = std::max(tl.xhi, pr.first);
+                }
             tiles.push_back(tl);
         }
         ntile[b] = (int)tiles.size() - tile0[b];
@@ -634,6 +645,27 @@ ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t pre
     CKC(upload(sys, &d_xw, xw));
     c.xidx = d_xidx;
     c.xw = d_xw;
+    sys->has_excl = !xidx.empty();
+    if (sys->has_excl && precision == FFMIN_MIXED) {  // per-atom scaled partners for the FP32 sweeps
+        std::vector<int32_t> xs_off(total + 1, 0), xs_part;
+        std::vector<float> xs_val;
+        for (int64_t a = 0; a < total; a++) {
+            xs_off[a] = (int32_t)xs_part.size();
+            for (const auto &pr : xs_lists[a]) {
+                xs_part.push_back(pr.first);
+                xs_val.push_back(pr.second);
+            }
+        }
+        xs_off[total] = (int32_t)xs_part.size();
+        int32_t *d_xs_off, *d_xs_part;
+        float *d_xs_val;
+        CKC(upload(sys, &d_xs_off, xs_off));
+        CKC(upload(sys, &d_xs_part, xs_part));
+        CKC(upload(sys, &d_xs_val, xs_val));
+        c.xs_off = d_xs_off;
+        c.xs_part = d_xs_part;
+        c.xs_val = d_xs_val;
+    }
     int32_t *d_term_sys;
     CKC(upload(sys, &d_term_sys, term_sys));
     c.term_sys = d_term_sys;
@@ -893,6 +925,9 @@ static ffmin_status check_options(ffmin_system *sys, const ffmin_options *o) {
         return fail(sys, FFMIN_ERR_INVALID_ARG, "gradfree_taylor_r must be >= 0");
     if (o->method == FFMIN_GRADFREE && (o->gradfree_parts < 0 || !(o->gradfree_margin >= 0.0)))
         return fail(sys, FFMIN_ERR_INVALID_ARG, "GRADFREE needs gradfree_parts >= 0 and gradfree_margin >= 0");
+    if (o->method == FFMIN_GRADFREE && sys->has_excl && sys->prec == FFMIN_MIXED)
+        return fail(sys, FFMIN_ERR_INVALID_ARG,
+                    "GRADFREE with exclusions needs FFMIN_FP64 (its FP32 rows do not mask the excluded pairs)");
     if (o->method == FFMIN_GRADFREE && (sys->n_sys != 1 || !(o->gradfree_delta > 0.0)))
         return fail(sys, FFMIN_ERR_INVALID_ARG, "GRADFREE needs one system and delta > 0");
     if (o->use_learned_precond && !sys->have_precond)

@@ -283,6 +283,13 @@ __device__ inline void bonded_item(const Ctx &c, int t0, int nt, int mode) {
         else { type = 3; term = t - c.n_bonds - c.n_angles - c.n_dihedrals; }
         double g[4][3];
         const bool grad = S.ev_kind == EV_EG;
+        if (type == 3 && mode == 0) {  // FP32 sweeps scale the excluded pairs themselves
+            c.te[t] = 0.0;
+            if (grad)
+                for (int p = 0; p < 2; p++)
+                    for (int k = 0; k < 3; k++) c.tg[3 * bonded_grad_slot(c, 3, term, p) + k] = 0.0;
+            continue;
+        }
         c.te[t] = bonded_term_all(c, x, type, term, grad ? g : nullptr);
         if (grad) {
             const int np = type == 3 ? 2 : type + 2;

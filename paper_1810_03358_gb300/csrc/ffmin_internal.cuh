@@ -66,8 +66,10 @@ constexpr int BONDED_ITEM_TERMS = 64;
 
 // item0 / nitem: the tile's items in the row-sweep list; row64: its first
 // item in the symmetric list (row of tile pairs (tile, J >= tile)), chunk64:
-// j-tiles per symmetric item of its system, tloc: index inside its system
-struct Tile { int32_t sys, a0, na, item0, nitem, row64, chunk64, tloc; };
+// j-tiles per symmetric item of its system, tloc: index inside its system;
+// xlo / xhi: the smallest and largest scaled partner (exclusion variant) of
+// its atoms, xlo > xhi when there is none
+struct Tile { int32_t sys, a0, na, item0, nitem, row64, chunk64, tloc, xlo, xhi, pad0, pad1; };
 
 struct DirOp {
     int32_t on, use_d, dots;  // dots: 1 -> |R|^2, <G,R>; 2 -> <Y_j, R> for the Y list
@@ -171,6 +173,11 @@ struct Ctx {
     int32_t n_dihedrals, n_excl;  // n_excl: exclusion corrections (type 3, after the dihedrals)
     const int2 *xidx;             // [n_excl] atom pair of each correction
     const double *xw;             // [n_excl] weight s_ij - 1 of its pair term
+    // the same scaled pairs per atom (CSR: partners of atom a in
+    // xs_part[xs_off[a] .. xs_off[a + 1]), scale s_ij in xs_val): the FP32
+    // sweeps scale those pairs inside their sums (MIXED objects only)
+    const int32_t *xs_off, *xs_part;
+    const float *xs_val;
     const int32_t *term_sys;  // [n_terms] system of each bonded term
     const int2 *sys_items;  // [n_sys] (first, count) of each system's work items (contiguous)
     // FP64 pair terms: sym64 = 1 evaluates each unordered pair once

@@ -50,16 +50,29 @@ template <> struct VT<double> {
     static __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 };
 
+// scale of the pair (i, j) in the exclusion variant (1 for every pair not
+// listed); i must be a real atom
+__device__ __forceinline__ float pair_xscale(const Ctx &c, int i, int j) {
+    float s = 1.f;
+    for (int m = c.xs_off[i]; m < c.xs_off[i + 1]; m++)
+        if (c.xs_part[m] == j) s = c.xs_val[m];
+    return s;
+}
+
 // IPT i-atoms per thread share every j load from shared memory.  DM: 0 an
 // off-diagonal tile; 1 the i-tile itself (j == i skipped); 2 the i-tile
-// itself on the symmetric list (only j > i: each pair once)
-template <typename T, int IPT, bool GRAD, int DM>
+// itself on the symmetric list (only j > i: each pair once).  MASK: the j
+// tile holds scaled partners of the i tile (exclusion variant, FP32): every
+// pair is multiplied by its scale s_ij inside the sums (ig: the i atoms'
+// global indices, -1 for padding; jt: the j tile's first atom).
+template <typename T, int IPT, bool GRAD, int DM, bool MASK = false>
 __device__ __forceinline__ void sweep(const typename VT<T>::V4 *__restrict__ sp,
                                       const typename VT<T>::V2 *__restrict__ sq,
                                       const typename VT<T>::V4 (&pi)[IPT],
                                       const typename VT<T>::V2 (&ci)[IPT], const int (&dk)[IPT],
                                       T (&gx)[IPT], T (&gy)[IPT], T (&gz)[IPT], T (&ec)[IPT],
-                                      T (&lj)[IPT]) {
+                                      T (&lj)[IPT], const Ctx *cx = nullptr, const int *ig = nullptr,
+                                      int jt = 0) {
 #pragma unroll 8
     for (int k = 0; k < TJ; k++) {
         const typename VT<T>::V4 pj = sp[k];
@@ -71,10 +84,15 @@ __device__ __forceinline__ void sweep(const typename VT<T>::V4 *__restrict__ sp,
             T ri = VT<T>::rsq(r2);
             if (DM == 1) ri = (k == dk[u]) ? T(0) : ri;
             if (DM == 2) ri = (k <= dk[u]) ? T(0) : ri;
+            T sc = T(1);
+            if (MASK) {
+                if (ig[u] >= 0) sc = (T)pair_xscale(*cx, ig[u], jt + k);
+            }
             const T ri2 = ri * ri;
-            const T e = pi[u].w * pj.w * ri;
+            const T e = MASK ? pi[u].w * pj.w * sc * ri : pi[u].w * pj.w * ri;
             const T ri6 = ri2 * ri2 * ri2;
-            const T c6 = ci[u].x * qj.x, c12 = ci[u].y * qj.y;
+            const T c6 = MASK ? ci[u].x * qj.x * sc : ci[u].x * qj.x;
+            const T c12 = MASK ? ci[u].y * qj.y * sc : ci[u].y * qj.y;
             const T t1 = c12 * ri6 - c6;
             ec[u] += e;
             lj[u] += ri6 * t1;
@@ -101,11 +119,12 @@ __device__ __forceinline__ void sweep(const typename VT<T>::V4 *__restrict__ sp,
 // e_cul + 6 e_lj, whose rounding error is relative to the difference, not to
 // the energies (FP32 coordinates of the trial point would add noise of order
 // u |x| |F| per pair, larger than the line search's energy decrements).
-template <int IPT, int DM>
+template <int IPT, int DM, bool MASK = false>
 __device__ __forceinline__ void sweep_delta(const float4 *__restrict__ sp, const float2 *__restrict__ sq,
                                             const float4 *__restrict__ sd, const float4 (&pi)[IPT],
                                             const float2 (&ci)[IPT], const float4 (&di)[IPT],
-                                            const int (&dk)[IPT], float (&ec)[IPT], float (&lj)[IPT]) {
+                                            const int (&dk)[IPT], float (&ec)[IPT], float (&lj)[IPT],
+                                            const Ctx *cx = nullptr, const int *ig = nullptr, int jt = 0) {
 #pragma unroll 4
     for (int k = 0; k < TJ; k++) {
         const float4 pj = sp[k];
@@ -128,8 +147,13 @@ __device__ __forceinline__ void sweep_delta(const float4 *__restrict__ sp, const
             const float ri4 = ri2 * ri2, rp4 = rp2 * rp2;
             const float d6 = X * (rp4 + rp2 * ri2 + ri4);
             const float d12 = d6 * (rp4 * rp2 + ri4 * ri2);
-            const float c6 = ci[u].x * qj.x, c12 = ci[u].y * qj.y;
-            ec[u] += pi[u].w * pj.w * d1;
+            float sc = 1.f;
+            if (MASK) {
+                if (ig[u] >= 0) sc = pair_xscale(*cx, ig[u], jt + k);
+            }
+            const float c6 = MASK ? ci[u].x * qj.x * sc : ci[u].x * qj.x;
+            const float c12 = MASK ? ci[u].y * qj.y * sc : ci[u].y * qj.y;
+            ec[u] += MASK ? pi[u].w * pj.w * sc * d1 : pi[u].w * pj.w * d1;
             lj[u] += c12 * d12 - c6 * d6;
         }
     }
@@ -261,7 +285,27 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? FFMIN_F32_MINBLOCKS : 8)
             for (int u = 0; u < IPT; u++) dk[u] = ig[u] - jt;
             bool done = false;
             if constexpr (MODE == 0) {
-                if (delta) {
+                // exclusion variant: this j tile holds scaled partners of
+                // the i tile (near the diagonal of a chain); -1 marks padding
+                const bool masked = c.xs_off != nullptr && tl.xlo <= tl.xhi && tl.xhi >= jt && tl.xlo < jt + TJ;
+                int igm[IPT];
+#pragma unroll
+                for (int u = 0; u < IPT; u++) igm[u] = tid + u * NT < tl.na ? ig[u] : -1;
+                if (masked) {
+                    if (delta) {
+                        if (diag && sym) sweep_delta<IPT, 2, true>(sp, sq, sd, pi, ci, di, dk, ec, lj, &c, igm, jt);
+                        else if (diag) sweep_delta<IPT, 1, true>(sp, sq, sd, pi, ci, di, dk, ec, lj, &c, igm, jt);
+                        else sweep_delta<IPT, 0, true>(sp, sq, sd, pi, ci, di, dk, ec, lj, &c, igm, jt);
+                    } else if (kind == EV_EG) {
+                        if (diag) sweep<T, IPT, true, 1, true>(sp, sq, pi, ci, dk, gx, gy, gz, ec, lj, &c, igm, jt);
+                        else sweep<T, IPT, true, 0, true>(sp, sq, pi, ci, dk, gx, gy, gz, ec, lj, &c, igm, jt);
+                    } else {
+                        if (diag && sym) sweep<T, IPT, false, 2, true>(sp, sq, pi, ci, dk, gx, gy, gz, ec, lj, &c, igm, jt);
+                        else if (diag) sweep<T, IPT, false, 1, true>(sp, sq, pi, ci, dk, gx, gy, gz, ec, lj, &c, igm, jt);
+                        else sweep<T, IPT, false, 0, true>(sp, sq, pi, ci, dk, gx, gy, gz, ec, lj, &c, igm, jt);
+                    }
+                    done = true;
+                } else if (delta) {
                     if (diag && sym) sweep_delta<IPT, 2>(sp, sq, sd, pi, ci, di, dk, ec, lj);
                     else if (diag) sweep_delta<IPT, 1>(sp, sq, sd, pi, ci, di, dk, ec, lj);
                     else sweep_delta<IPT, 0>(sp, sq, sd, pi, ci, di, dk, ec, lj);
