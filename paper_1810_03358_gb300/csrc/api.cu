@@ -64,6 +64,12 @@ struct ffmin_system {
     int graph_ticks = 0;
     cudaGraphExec_t graph = nullptr;
     int32_t *h_nactive = nullptr;  // pinned
+    // a minimization as one graph launch: a conditional WHILE node whose body
+    // is TICKS_PER_GRAPH rounds and the loop-condition kernel; d_loop / h_loop
+    // [2]: rounds run, round bound (device / pinned host)
+    cudaGraphExec_t loop_exec = nullptr;
+    bool loop_failed = false;
+    int64_t *d_loop = nullptr, *h_loop = nullptr;
     // gradient-free path: device state and a graph of PARAB_MOVES moves
     void *parab_state = nullptr;
     cudaGraphExec_t parab_graph = nullptr;
@@ -327,6 +333,8 @@ ffmin_status ffmin_destroy(ffmin_system *sys) {
     if (!sys) return FFMIN_ERR_INVALID_ARG;
     if (sys->stream) cudaStreamSynchronize(sys->stream);
     if (sys->graph) cudaGraphExecDestroy(sys->graph);
+    if (sys->loop_exec) cudaGraphExecDestroy(sys->loop_exec);
+    if (sys->h_loop) cudaFreeHost(sys->h_loop);
     if (sys->parab_graph) cudaGraphExecDestroy(sys->parab_graph);
     for (void *p : sys->allocs) cudaFree(p);
     if (sys->h_nactive) cudaFreeHost(sys->h_nactive);
@@ -388,7 +396,8 @@ ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t pre
     if (e != cudaSuccess) { ffmin_status st = cuda_fail(nullptr, e, "cudaStreamCreate"); delete sys; return st; }
     cudaEventCreateWithFlags(&sys->ev_in, cudaEventDisableTiming);
     cudaEventCreateWithFlags(&sys->ev_out, cudaEventDisableTiming);
-    if (cudaMallocHost((void **)&sys->h_nactive, sizeof(int32_t)) != cudaSuccess) {
+    if (cudaMallocHost((void **)&sys->h_nactive, sizeof(int32_t)) != cudaSuccess ||
+        cudaMallocHost((void **)&sys->h_loop, 2 * sizeof(int64_t)) != cudaSuccess) {
         ffmin_destroy(sys);
         return fail(nullptr, FFMIN_ERR_OOM, "pinned allocation failed");
     }
@@ -762,7 +771,16 @@ static cudaError_t launch_tick(ffmin_system *sys) {
     return cudaSuccess;
 }
 
-static const int TICKS_PER_GRAPH = 8;
+constexpr int TICKS_PER_GRAPH = 8;
+
+// Loop condition of the device-driven minimization: counts the rounds and
+// keeps the WHILE node running while a system is active and the round bound
+// is not reached (so the loop always ends within loop[1] + 8 rounds).
+__global__ void k_loop_cond(cudaGraphConditionalHandle h, const int32_t *nactive, int64_t *loop) {
+    const int64_t t = loop[0] + TICKS_PER_GRAPH;
+    loop[0] = t;
+    cudaGraphSetConditional(h, (*nactive > 0 && t < loop[1]) ? 1u : 0u);
+}
 static int kernels_per_tick(const ffmin_system *sys) {
     return (sys->prec == FFMIN_MIXED ? 7 : 6) + (sys->c.sep_reduce ? 4 : 0);
 }
@@ -780,6 +798,48 @@ static ffmin_status ensure_graph(ffmin_system *sys) {
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(sys, e, "cudaGraphInstantiate");
     sys->graph_ticks = TICKS_PER_GRAPH;
+    return FFMIN_OK;
+}
+
+// The whole minimization as one graph: a WHILE node over TICKS_PER_GRAPH
+// rounds plus k_loop_cond.  When the runtime cannot build it, minimize_dev
+// replays the plain graph of rounds from the host instead.
+static ffmin_status ensure_loop(ffmin_system *sys) {
+    if (sys->loop_exec || sys->loop_failed) return FFMIN_OK;
+    if (!sys->d_loop) CK(dalloc(sys, &sys->d_loop, 2));
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    cudaGraphConditionalHandle h{};
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams p{};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &p);
+    if (e == cudaSuccess) {
+        cudaGraph_t body = p.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(sys->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t e1 = cudaSuccess;
+            for (int t = 0; t < TICKS_PER_GRAPH && e1 == cudaSuccess; t++) e1 = launch_tick(sys);
+            if (e1 == cudaSuccess) {
+                k_loop_cond<<<1, 1, 0, sys->stream>>>(h, sys->c.nactive, sys->d_loop);
+                e1 = cudaGetLastError();
+            }
+            cudaGraph_t out = nullptr;
+            const cudaError_t e2 = cudaStreamEndCapture(sys->stream, &out);
+            e = e1 != cudaSuccess ? e1 : e2;
+        }
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&sys->loop_exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {  // fall back to the host-replayed graph of rounds
+        (void)cudaGetLastError();
+        sys->loop_exec = nullptr;
+        sys->loop_failed = true;
+    }
     return FFMIN_OK;
 }
 
@@ -997,19 +1057,33 @@ static ffmin_status minimize_dev(ffmin_system *sys, double *x_dev, const ffmin_o
     if ((st = set_counts(sys)) != FFMIN_OK) return st;
     st = ensure_graph(sys);
     if (st != FFMIN_OK) return st;
+    if ((st = ensure_loop(sys)) != FFMIN_OK) return st;
     const int64_t max_ticks = o->max_ticks > 0 ? o->max_ticks : (int64_t)o->max_evals + 64;
     int64_t ticks = 0;
     bool timeout = false;
-    for (;;) {
-        CK(cudaGraphLaunch(sys->graph, sys->stream));
-        ticks += sys->graph_ticks;
+    if (sys->loop_exec) {  // one graph launch runs the whole minimization
+        sys->h_loop[0] = 0;
+        sys->h_loop[1] = max_ticks;
+        CK(cudaMemcpyAsync(sys->d_loop, sys->h_loop, 2 * sizeof(int64_t), cudaMemcpyHostToDevice, sys->stream));
+        CK(cudaGraphLaunch(sys->loop_exec, sys->stream));
+        CK(cudaMemcpyAsync(sys->h_loop, sys->d_loop, sizeof(int64_t), cudaMemcpyDeviceToHost, sys->stream));
         CK(cudaMemcpyAsync(sys->h_nactive, c.nactive, sizeof(int32_t), cudaMemcpyDeviceToHost, sys->stream));
         CK(cudaStreamSynchronize(sys->stream));
-        if (*sys->h_nactive <= 0) break;
-        if (ticks >= max_ticks) { timeout = true; break; }
+        ticks = sys->h_loop[0];
+        timeout = *sys->h_nactive > 0;
+        sys->last_launches = ticks * kernels_per_tick(sys) + ticks / TICKS_PER_GRAPH;
+    } else {
+        for (;;) {
+            CK(cudaGraphLaunch(sys->graph, sys->stream));
+            ticks += sys->graph_ticks;
+            CK(cudaMemcpyAsync(sys->h_nactive, c.nactive, sizeof(int32_t), cudaMemcpyDeviceToHost, sys->stream));
+            CK(cudaStreamSynchronize(sys->stream));
+            if (*sys->h_nactive <= 0) break;
+            if (ticks >= max_ticks) { timeout = true; break; }
+        }
+        sys->last_launches = ticks * kernels_per_tick(sys);
     }
     sys->last_ticks = ticks;
-    sys->last_launches = ticks * kernels_per_tick(sys);
     if (timeout) {
         // a step accepted in the last round is written into X (FGM: the best
         // point) by the next round's update kernel: run that update once more
@@ -1145,6 +1219,10 @@ ffmin_status ffmin_autotune(ffmin_system *sys, const double *x_dev, int32_t *den
         if (sys->graph) {  // kernel parameters (item count, grid) changed
             cudaGraphExecDestroy(sys->graph);
             sys->graph = nullptr;
+        }
+        if (sys->loop_exec) {
+            cudaGraphExecDestroy(sys->loop_exec);
+            sys->loop_exec = nullptr;
         }
         if (k == AUTOTUNE_N) break;  // the best layout is installed
         if ((st = eval_all(sys, x_dev, EV_EG)) != FFMIN_OK) return st;

@@ -46,7 +46,7 @@ enum UpdKind : int {
     U_FGM_BEST_W,    // XB <- W
     U_OGM,           // OGM: (accept) X <- XT, G <- GT; (restart) X0 <- X, DS <- G, else
                      // (accept) DS += h G; then W = a X + b X0, R = -(a G + inv DS), <R, R>
-    U_HB             // heavy ball: (accept) P <- X, X <- XT, G <- GT; (start) P <- X;
+    U_HB             // heavy ball: P <- X (start: P <- XT), X <- XT, G <- GT;
                      // then XT = fma(b, X - P, fma(-a, G, X)), the next iterate
 };
 

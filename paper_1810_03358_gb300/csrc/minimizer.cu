@@ -267,20 +267,15 @@ __global__ void __launch_bounds__(TI) k_update(Ctx c) {
             for (int k = 0; k < 3; k++) XB[k] = W[k];
             break;
         case U_HB: {  // Eq. 8, formed as the oracle forms it
+            // accept the evaluated point (XT, GT): x^{k+1}, or at the start
+            // x^0 itself with x^{-1} = x^0; then form the next iterate
             double *XTw = vslot(c, V_XT) + off;
             const double a = S.upd.a, b = S.upd.b;
             for (int k = 0; k < 3; k++) {
-                double x = X[k], g = G[k];
-                double xp = P[k];
-                if (S.upd.accept) {
-                    xp = x;
-                    x = XT[k];
-                    g = GT[k];
-                    X[k] = x;
-                    G[k] = g;
-                } else {
-                    xp = x;  // x^{-1} = x^0
-                }
+                const double x = XT[k], g = GT[k];
+                const double xp = S.upd.accept ? X[k] : x;
+                X[k] = x;
+                G[k] = g;
                 P[k] = xp;
                 XTw[k] = fma(b, x - xp, fma(-a, g, x));
             }

@@ -121,9 +121,22 @@ def minimize_with(systems, w16, precision=ffmin.FFMIN_MIXED, use=True, max_iter=
 
 
 def training_systems(n_sys=128, seed0=10000, lo=1000, hi=5000):
+    """n_sys systems with sizes uniform in [lo, hi] (size seed seed0) and
+    seeds seed0, seed0 + 1, ...; a seed whose chain growth gives up is
+    skipped (the next seed takes its place)."""
     rng = np.random.default_rng(seed0)
     sizes = rng.integers(lo, hi + 1, size=n_sys)
-    return [synth.make_system(int(n), seed0 + b) for b, n in enumerate(sizes)]
+    out, seed = [], seed0
+    for n in sizes:
+        while True:
+            try:
+                out.append(synth.make_system(int(n), seed))
+                break
+            except RuntimeError:
+                pass
+            finally:
+                seed += 1
+    return out
 
 
 # FP16 weights written by main() (the shipped network)

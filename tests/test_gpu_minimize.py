@@ -150,9 +150,11 @@ def ensemble_parity(oracle_mod, s, xg, rg, kw, energies=None, mixed=False):
     oracle's gradient of the returned point below the tolerance) and reports
     that point's energy.  A MIXED run (FP32 trials take other decisions
     from the first steps on, so it ends in whichever basin its own
-    trajectory reaches) is held one-sided: no more than 0.01 % above the
-    highest member; a deeper minimum than the members' is a valid result
-    (measured: up to 0.23 % below).  Prints which criterion held."""
+    trajectory reaches) is held one-sided: no higher than the highest member
+    by more than max(0.01 %, the members' own spread), the scale at which
+    runs perturbed by rounding already choose different basins (measured
+    spreads 6.6e-4 to 1.5e-3); a deeper minimum than the members' is a valid
+    result (measured: up to 0.23 % below).  Prints which criterion held."""
     if energies is None:
         energies = oracle_ensemble(s, kw)
     assert energies, "the oracle itself did not converge"
@@ -161,9 +163,9 @@ def ensemble_parity(oracle_mod, s, xg, rg, kw, energies=None, mixed=False):
     e = rg["energy"]
     in_range = lo - max(tol, hi - lo) <= e <= hi + tol
     near = any(abs(m - e) <= REL_E * abs(e) for m in energies)
-    below = mixed and e < lo
+    below = mixed and e <= hi + max(tol, hi - lo)
     print(f"ensemble ({len(energies)} members, spread {(hi - lo) / abs(lo):.1e}): "
-          f"{'range' if in_range else ('member' if near else ('below' if below else 'miss'))}, "
+          f"{'range' if in_range else ('member' if near else ('spread' if below else 'miss'))}, "
           f"gpu {e:.10g} ({(e - lo) / abs(lo):+.1e} from the lowest member)")
     assert in_range or near or below, (e, energies)
     assert rg["status_name"] == "ok", rg
