@@ -159,6 +159,69 @@ __device__ __forceinline__ void sweep_delta(const float4 *__restrict__ sp, const
     }
 }
 
+// Energy-only forms with the i atom's factors outside the sums: per i the
+// sums of q'_j X1, c6_j X6 and c12_j X12 (X = r^-1, r^-6, r^-12 for a plain
+// energy; the exact differences r'^-1 - r^-1, ... for a difference trial),
+// combined with q'_i, c6_i, c12_i once per item.  fa, f6, f12 accumulate
+// across the item's j tiles.
+template <int IPT, int DM>
+__device__ __forceinline__ void sweep_e_factored(const float4 *__restrict__ sp, const float2 *__restrict__ sq,
+                                                 const float4 (&pi)[IPT], const int (&dk)[IPT], float (&fa)[IPT],
+                                                 float (&f6)[IPT], float (&f12)[IPT]) {
+#pragma unroll 8
+    for (int k = 0; k < TJ; k++) {
+        const float4 pj = sp[k];
+        const float2 qj = sq[k];
+#pragma unroll
+        for (int u = 0; u < IPT; u++) {
+            const float dx = pj.x - pi[u].x, dy = pj.y - pi[u].y, dz = pj.z - pi[u].z;
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            float ri = rsqrt_approx(r2);
+            if (DM == 1) ri = (k == dk[u]) ? 0.f : ri;
+            if (DM == 2) ri = (k <= dk[u]) ? 0.f : ri;
+            const float ri2 = ri * ri;
+            const float ri6 = ri2 * ri2 * ri2;
+            fa[u] = fmaf(pj.w, ri, fa[u]);
+            f6[u] = fmaf(qj.x, ri6, f6[u]);
+            f12[u] = fmaf(qj.y, ri6 * ri6, f12[u]);
+        }
+    }
+}
+
+template <int IPT, int DM>
+__device__ __forceinline__ void sweep_delta_factored(const float4 *__restrict__ sp, const float2 *__restrict__ sq,
+                                                     const float4 *__restrict__ sd, const float4 (&pi)[IPT],
+                                                     const float4 (&di)[IPT], const int (&dk)[IPT],
+                                                     float (&fa)[IPT], float (&f6)[IPT], float (&f12)[IPT]) {
+#pragma unroll 4
+    for (int k = 0; k < TJ; k++) {
+        const float4 pj = sp[k];
+        const float2 qj = sq[k];
+        const float4 dj = sd[k];
+#pragma unroll
+        for (int u = 0; u < IPT; u++) {
+            const float dx = pj.x - pi[u].x, dy = pj.y - pi[u].y, dz = pj.z - pi[u].z;
+            const float ex = dj.x - di[u].x, ey = dj.y - di[u].y, ez = dj.z - di[u].z;
+            float r2 = dx * dx + dy * dy + dz * dz;
+            if (DM != 0) r2 = (k == dk[u]) ? 1.f : r2;  // j == i: dd = 0, every difference vanishes
+            float D = ex * (2.f * dx + ex) + ey * (2.f * dy + ey) + ez * (2.f * dz + ez);
+            if (DM == 2) D = (k <= dk[u]) ? 0.f : D;  // each pair once: j < i contributes nothing
+            const float ri = rsqrt_approx(r2), rp = rsqrt_approx(r2 + D);
+            const float ri2 = ri * ri, rp2 = rp * rp;
+            const float X = -D * ri2 * rp2;
+            float inv;
+            asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv) : "f"(ri + rp));
+            const float d1 = X * inv;
+            const float ri4 = ri2 * ri2, rp4 = rp2 * rp2;
+            const float d6 = X * (rp4 + rp2 * ri2 + ri4);
+            const float d12 = d6 * (rp4 * rp2 + ri4 * ri2);
+            fa[u] = fmaf(pj.w, d1, fa[u]);
+            f6[u] = fmaf(qj.x, d6, f6[u]);
+            f12[u] = fmaf(qj.y, d12, f12[u]);
+        }
+    }
+}
+
 // NT threads per block, IPT i-atoms per thread, NT * IPT == TI (one tile).
 // Register caps: the FP32 kernel (2 i-atoms per thread) runs at 12 resident
 // 64-thread blocks per SM (80 registers; measured on GB300 faster than 16
@@ -305,14 +368,15 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? FFMIN_F32_MINBLOCKS : 8)
                         else sweep<T, IPT, false, 0, true>(sp, sq, pi, ci, dk, gx, gy, gz, ec, lj, &c, igm, jt);
                     }
                     done = true;
-                } else if (delta) {
-                    if (diag && sym) sweep_delta<IPT, 2>(sp, sq, sd, pi, ci, di, dk, ec, lj);
-                    else if (diag) sweep_delta<IPT, 1>(sp, sq, sd, pi, ci, di, dk, ec, lj);
-                    else sweep_delta<IPT, 0>(sp, sq, sd, pi, ci, di, dk, ec, lj);
+                } else if (delta) {  // factored sums in the (idle) gradient registers
+                    if (diag && sym) sweep_delta_factored<IPT, 2>(sp, sq, sd, pi, di, dk, gx, gy, gz);
+                    else if (diag) sweep_delta_factored<IPT, 1>(sp, sq, sd, pi, di, dk, gx, gy, gz);
+                    else sweep_delta_factored<IPT, 0>(sp, sq, sd, pi, di, dk, gx, gy, gz);
                     done = true;
-                } else if (sym) {
-                    if (diag) sweep<T, IPT, false, 2>(sp, sq, pi, ci, dk, gx, gy, gz, ec, lj);
-                    else sweep<T, IPT, false, 0>(sp, sq, pi, ci, dk, gx, gy, gz, ec, lj);
+                } else if (kind == EV_E) {
+                    if (diag && sym) sweep_e_factored<IPT, 2>(sp, sq, pi, dk, gx, gy, gz);
+                    else if (diag) sweep_e_factored<IPT, 1>(sp, sq, pi, dk, gx, gy, gz);
+                    else sweep_e_factored<IPT, 0>(sp, sq, pi, dk, gx, gy, gz);
                     done = true;
                 }
             }
@@ -331,11 +395,20 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? FFMIN_F32_MINBLOCKS : 8)
         if constexpr (MODE == 0) {
             if (sym) dst = c.gpf_sym + (int64_t)I.slot * TI;
         }
+        // FP32 energy only: masked tiles summed the pair terms into ec / lj,
+        // the others the factored sums into gx, gy, gz
+        const bool factored = MODE == 0 && kind == EV_E;
 #pragma unroll
         for (int u = 0; u < IPT; u++) {
             V4 o;
-            o.x = gx[u]; o.y = gy[u]; o.z = gz[u];
-            o.w = ec[u] + lj[u] * T(1.0 / 6.0);
+            if (factored) {
+                o.x = T(0); o.y = T(0); o.z = T(0);
+                o.w = ec[u] + lj[u] * T(1.0 / 6.0) + pi[u].w * gx[u] +
+                      (ci[u].y * gz[u] - ci[u].x * gy[u]) * T(1.0 / 6.0);
+            } else {
+                o.x = gx[u]; o.y = gy[u]; o.z = gz[u];
+                o.w = ec[u] + lj[u] * T(1.0 / 6.0);
+            }
             dst[tid + u * NT] = o;
         }
     }
@@ -403,6 +476,7 @@ __global__ void __launch_bounds__(NT_SYM, 6) k_pair64_sym(Ctx c) {
             ci = make_double2(0.0, 0.0);
         }
         double gx = 0.0, gy = 0.0, gz = 0.0, ec = 0.0, lj = 0.0;
+        double sc1 = 0.0, s6 = 0.0, s12 = 0.0;  // energy-only factored sums
         const int jend = I.j0 + I.nj;
         for (int jt = I.j0; jt < jend; jt += TJ) {
             const int jl = jt + tid;
@@ -422,6 +496,26 @@ __global__ void __launch_bounds__(NT_SYM, 6) k_pair64_sym(Ctx c) {
             // k = 1 .. TJ/2 (at k = TJ/2 only t < TJ/2); other tiles every k
             const bool diag = I.diag && jt == I.j0;
             const int k0 = diag ? 1 : 0, k1 = diag ? TJ / 2 : TJ - 1;
+            if (!grad) {
+                // energy only: the i atom's factors leave the sums,
+                // E_i = q'_i sum q'_j / r + (c12_i sum c12_j r^-12 - c6_i sum c6_j r^-6) / 6
+                for (int k = k0; k <= k1; k++) {
+                    if (diag && k == TJ / 2 && tid >= TJ / 2) break;  // warp-uniform
+                    const int j = (tid + k) & (TJ - 1);
+                    const double4_32a pj = sp[j];
+                    const double2 qj = sq[j];
+                    const double dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+                    const double r2 = dx * dx + dy * dy + dz * dz;
+                    const double ri = rsqrt(r2);
+                    const double ri2 = ri * ri;
+                    const double ri6 = ri2 * ri2 * ri2;
+                    sc1 = fma(pj.w, ri, sc1);
+                    s6 = fma(qj.x, ri6, s6);
+                    s12 = fma(qj.y, ri6 * ri6, s12);
+                }
+                __syncthreads();
+                continue;
+            }
             for (int k = k0; k <= k1; k++) {
                 if (diag && k == TJ / 2 && tid >= TJ / 2) break;  // warp-uniform
                 const int j = (tid + k) & (TJ - 1);
@@ -462,7 +556,7 @@ __global__ void __launch_bounds__(NT_SYM, 6) k_pair64_sym(Ctx c) {
         }
         double4_32a o;
         o.x = gx; o.y = gy; o.z = gz;
-        o.w = ec + lj * (1.0 / 6.0);
+        o.w = grad ? ec + lj * (1.0 / 6.0) : pi.w * sc1 + (ci.y * s12 - ci.x * s6) * (1.0 / 6.0);
         c.gpd[(int64_t)I.slot * TI + tid] = o;
     }
 }

@@ -83,7 +83,9 @@ def check_mixed(ffmin, oracle_mod, systems, xs=None):
         bar = 1e-5 + mixed_position_bound(xs[b])
         assert abs(e[b] - d["total"]) <= bar * d["sum_abs"], (b, e[b], d["total"], bar)
         assert abs(e_only[b] - d["total"]) <= bar * d["sum_abs"], (b, e_only[b], d["total"])
-        assert np.abs(g[b] - go).max() <= 1e-4 * np.abs(go).max(), b
+        # near a minimum the force scale is the stopping tolerance: the bar is
+        # then 2 % of it in absolute terms (as for the plain MIXED path)
+        assert np.abs(g[b] - go).max() <= max(1e-4 * np.abs(go).max(), 0.02 * 0.1), b
 
 
 @pytest.mark.parametrize("n", [3, 4, 64, 129, 300, 1000])
