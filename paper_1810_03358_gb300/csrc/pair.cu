@@ -73,7 +73,8 @@ __device__ __forceinline__ void sweep(const typename VT<T>::V4 *__restrict__ sp,
                                       T (&gx)[IPT], T (&gy)[IPT], T (&gz)[IPT], T (&ec)[IPT],
                                       T (&lj)[IPT], const Ctx *cx = nullptr, const int *ig = nullptr,
                                       int jt = 0) {
-#pragma unroll 8
+    // the masked form runs on a few tiles only: kept rolled (smaller kernel)
+#pragma unroll(MASK ? 1 : 8)
     for (int k = 0; k < TJ; k++) {
         const typename VT<T>::V4 pj = sp[k];
         const typename VT<T>::V2 qj = sq[k];
@@ -125,7 +126,7 @@ __device__ __forceinline__ void sweep_delta(const float4 *__restrict__ sp, const
                                             const float2 (&ci)[IPT], const float4 (&di)[IPT],
                                             const int (&dk)[IPT], float (&ec)[IPT], float (&lj)[IPT],
                                             const Ctx *cx = nullptr, const int *ig = nullptr, int jt = 0) {
-#pragma unroll 4
+#pragma unroll(MASK ? 1 : 4)
     for (int k = 0; k < TJ; k++) {
         const float4 pj = sp[k];
         const float2 qj = sq[k];
@@ -235,9 +236,12 @@ __device__ __forceinline__ void sweep_delta_factored(const float4 *__restrict__ 
 #ifndef FFMIN_F32_MINBLOCKS
 #define FFMIN_F32_MINBLOCKS (768 / TI * FFMIN_F32_IPT)
 #endif
-template <typename T, int NT, int IPT>
+// XS: the object carries the exclusion variant (FP32 sweeps scale the listed
+// pairs); a separate instantiation keeps the masked code out of the kernel
+// every other object runs
+template <typename T, int NT, int IPT, bool XS = false>
 __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? FFMIN_F32_MINBLOCKS : 8)) k_pair(Ctx c);
-template <typename T, int NT, int IPT>
+template <typename T, int NT, int IPT, bool XS>
 __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? FFMIN_F32_MINBLOCKS : 8)) k_pair(Ctx c) {
     static_assert(NT * IPT == TI, "a block covers one i-tile");
     using V4 = typename VT<T>::V4;
@@ -350,7 +354,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? FFMIN_F32_MINBLOCKS : 8)
             if constexpr (MODE == 0) {
                 // exclusion variant: this j tile holds scaled partners of
                 // the i tile (near the diagonal of a chain); -1 marks padding
-                const bool masked = c.xs_off != nullptr && tl.xlo <= tl.xhi && tl.xhi >= jt && tl.xlo < jt + TJ;
+                const bool masked = XS && tl.xlo <= tl.xhi && tl.xhi >= jt && tl.xlo < jt + TJ;
                 int igm[IPT];
 #pragma unroll
                 for (int u = 0; u < IPT; u++) igm[u] = tid + u * NT < tl.na ? ig[u] : -1;
@@ -565,6 +569,7 @@ __global__ void __launch_bounds__(NT_SYM, 6) k_pair64_sym(Ctx c) {
 // per pair), FP64 one (the FP64 pipe, not the loads, is the limit)
 constexpr int NT_F32 = TI / FFMIN_F32_IPT, NT_F64 = 128;
 #define K_F32 k_pair<float, NT_F32, FFMIN_F32_IPT>
+#define K_F32X k_pair<float, NT_F32, FFMIN_F32_IPT, true>
 #define K_F64 k_pair<double, 128, 1>
 
 int pair_grid_size(int mode) {
@@ -637,7 +642,8 @@ __global__ void __launch_bounds__(256) k_activelist(Ctx c) {
 cudaError_t launch_pair(const Ctx &c, int grid32, int grid64, cudaStream_t s) {
     k_activelist<<<1, 256, 0, s>>>(c);  // also gives both pair kernels fresh work queues
     if (c.prec == FFMIN_MIXED) {
-        K_F32<<<grid32, NT_F32, 0, s>>>(c);
+        if (c.xs_off) K_F32X<<<grid32, NT_F32, 0, s>>>(c);
+        else K_F32<<<grid32, NT_F32, 0, s>>>(c);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
