@@ -1,10 +1,12 @@
 // C ABI of the ffmin library (declared in include/ffmin.h): creation of a
 // batch of systems, energy / gradient evaluation and the minimization driver.
 //
-// The driver keeps every decision on the device: it replays a CUDA graph of
-// TICKS pipeline rounds (update, two direction passes, prepare, pair,
-// finalize) on the library's own stream and reads back one counter of
-// still-active systems per replay.
+// The driver keeps every decision on the device: a minimization is one
+// launch of a CUDA graph whose conditional WHILE node repeats a body of
+// TICKS_PER_GRAPH pipeline rounds (update, two direction passes, prepare,
+// pair, finalize) until no system is active or the round bound is reached;
+// where the runtime cannot build that graph, the host replays the body graph
+// and reads back the count of still-active systems after each replay.
 #include <algorithm>
 #include <array>
 #include <limits>

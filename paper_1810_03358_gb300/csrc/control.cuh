@@ -5,8 +5,8 @@
 //     update -> direction 1 -> direction 2 -> prepare -> pair -> finalize
 // and evaluates at most one energy (E) or energy+gradient (EG) per system.
 // After each stage the machine consumes that stage's reductions and writes
-// the requests of the following stages, so a whole minimization runs as a
-// replayed CUDA graph of ticks with no host round trip per evaluation.
+// the requests of the following stages, so a whole minimization runs as one
+// graph launch of repeated ticks with no host round trip per evaluation.
 //
 // The machine restates, step for step, Algorithms 1-6 of arXiv 1810.03358
 // (Sections 5.1-5.2) and the adaptive gradient descent of Section 3 (Eq. 4),
