@@ -61,6 +61,9 @@ HW_SYM_EG, HW_SYM_E, HW_ROW_EG, HW_DELTA = 38.0, 21.0, 64.0, 40.0
 # nominal 1.25 TFLOP/s at 2,070 MHz)
 FP32_LANES_X2 = 152 * 128 * 2
 FP64_LANES_X2 = 152 * 2 * 2
+# minimizations replay their rounds from the host (--host-loop): the same
+# work, with every kernel visible to a kernel-level profiler
+HOST_LOOP = 0
 PROFILE_SUMMARY = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles",
                                "pair_kernels_30k.md")
 
@@ -177,7 +180,9 @@ def step_config(system=None):
     the generated inputs when the system is given."""
     out = {"workload": f"{N_ATOMS}-atom chain globule (seed {SEED}), plain FP64 path, "
                        f"L-BFGS m=10 capped at {CAP_ITERS} steps per step",
-           "n_atoms": N_ATOMS, "l2": "flushed (256 MB write) between steps"}
+           "n_atoms": N_ATOMS, "l2": "flushed (256 MB write) between steps",
+           "minimize_driver": ("host-replayed graph of 8 rounds" if HOST_LOOP else
+                               "one graph launch (conditional WHILE node over the rounds)")}
     if system is not None:
         from paper_1810_03358_gb300 import synth
         out["input_sha256"] = synth.digest(system)
@@ -216,7 +221,7 @@ def bench_gpu(args):
         evals = []
         for _ in range(warmup):
             x.copy_(x0)
-            S.minimize(x, method="LBFGS", lbfgs_m=10, max_iter=CAP_ITERS)
+            S.minimize(x, method="LBFGS", lbfgs_m=10, max_iter=CAP_ITERS, host_loop=HOST_LOOP)
         torch.cuda.synchronize()
         times = []
         launches = 0
@@ -228,14 +233,14 @@ def bench_gpu(args):
             if e2e:
                 t0 = time.perf_counter()
                 pin.copy_(torch.from_numpy(xh))
-                r = S.minimize_host(pin.numpy(), method="LBFGS", lbfgs_m=10, max_iter=CAP_ITERS)
+                r = S.minimize_host(pin.numpy(), method="LBFGS", lbfgs_m=10, max_iter=CAP_ITERS, host_loop=HOST_LOOP)
                 torch.cuda.synchronize()
                 times.append(time.perf_counter() - t0)
             else:
                 ev0 = torch.cuda.Event(enable_timing=True)
                 ev1 = torch.cuda.Event(enable_timing=True)
                 ev0.record()
-                r = S.minimize(x, method="LBFGS", lbfgs_m=10, max_iter=CAP_ITERS)
+                r = S.minimize(x, method="LBFGS", lbfgs_m=10, max_iter=CAP_ITERS, host_loop=HOST_LOOP)
                 ev1.record()
                 torch.cuda.synchronize()
                 times.append(ev0.elapsed_time(ev1) / 1e3)
@@ -635,11 +640,11 @@ def profile_run(args):
         systems = synth.make_batch(256)
         S = ffmin.System(systems, ffmin.FFMIN_MIXED)
         x = torch.tensor([v for s in systems for v in s.x.reshape(-1)], dtype=torch.float64, device="cuda")
-        S.minimize(x.clone(), method="LBFGS", max_iter=1)
+        S.minimize(x.clone(), method="LBFGS", max_iter=1, host_loop=HOST_LOOP)
         torch.cuda.synchronize()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record()
-        r = S.minimize(x.clone(), method="LBFGS", max_iter=args.profile_batch)
+        r = S.minimize(x.clone(), method="LBFGS", max_iter=args.profile_batch, host_loop=HOST_LOOP)
         ev1.record()
         torch.cuda.synchronize()
         st = S.last_stats()
@@ -676,7 +681,7 @@ def profile_run(args):
         S = ffmin.System(systems, ffmin.FFMIN_FP64)
         x = torch.tensor(np.concatenate([s.x.reshape(-1) for s in systems]), dtype=torch.float64,
                          device="cuda")
-        r = S.minimize(x.clone(), method="LBFGS", max_iter=args.profile_vectors)
+        r = S.minimize(x.clone(), method="LBFGS", max_iter=args.profile_vectors, host_loop=HOST_LOOP)
         torch.cuda.synchronize()
         print("profile-vectors", S.last_stats(), sorted({q["iterations"] for q in r}))
         S.close()
@@ -685,11 +690,11 @@ def profile_run(args):
         s = synth.make_system(3334, 2)
         x = torch.tensor(s.x.reshape(-1), dtype=torch.float64, device="cuda")
         S = ffmin.System([s], ffmin.FFMIN_MIXED)
-        S.minimize(x.clone(), method="LBFGS", max_iter=2)
+        S.minimize(x.clone(), method="LBFGS", max_iter=2, host_loop=HOST_LOOP)
         torch.cuda.synchronize()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record()
-        r = S.minimize(x.clone(), method="LBFGS", max_iter=args.profile_minimize)
+        r = S.minimize(x.clone(), method="LBFGS", max_iter=args.profile_minimize, host_loop=HOST_LOOP)
         ev1.record()
         torch.cuda.synchronize()
         st = S.last_stats()
@@ -729,7 +734,11 @@ def main():
     ap.add_argument("--profile-batch", type=int, default=0)
     ap.add_argument("--profile-vectors", type=int, default=0)
     ap.add_argument("--profile-epochs", type=int, default=0)
+    ap.add_argument("--host-loop", action="store_true",
+                    help="minimizations replay their rounds from the host (for kernel-level profiling)")
     args = ap.parse_args()
+    global HOST_LOOP
+    HOST_LOOP = int(args.host_loop)
     if args.profile:
         profile_run(args)
     elif args.impl == "reference":

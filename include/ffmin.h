@@ -162,6 +162,12 @@ typedef struct {
      * Taylor expansion about that position (Section 3's linearised far
      * field; Lennard-Jones stays exact); 0 (default): exact rows. */
     double gradfree_taylor_r;
+    /* 0 (default): a minimization is one launch of a CUDA graph whose
+     * conditional WHILE node repeats the pipeline rounds on the device.  1:
+     * the host replays the same rounds (a graph of 8) and checks for active
+     * systems after each replay: the same work and results, for profilers
+     * that cannot look into conditional graph nodes. */
+    int32_t host_loop;
 } ffmin_options;
 
 typedef struct {

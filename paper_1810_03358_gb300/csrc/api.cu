@@ -304,6 +304,7 @@ void ffmin_options_default(ffmin_options *o) {
     o->hb_alpha = 1e-4;
     o->hb_beta = 0.5;
     o->gradfree_taylor_r = 0.0;
+    o->host_loop = 0;
 }
 
 const char *ffmin_status_string(ffmin_status s) {
@@ -994,6 +995,7 @@ static ffmin_status check_options(ffmin_system *sys, const ffmin_options *o) {
         return fail(sys, FFMIN_ERR_INVALID_ARG, "GRADFREE needs one system and delta > 0");
     if (o->use_learned_precond && !sys->have_precond)
         return fail(sys, FFMIN_ERR_INVALID_ARG, "no preconditioner weights set");
+    if (o->host_loop != 0 && o->host_loop != 1) return fail(sys, FFMIN_ERR_INVALID_ARG, "host_loop must be 0 or 1");
     if (o->fgm_restart != 0 && o->fgm_restart != 1)
         return fail(sys, FFMIN_ERR_INVALID_ARG, "fgm_restart must be 0 or 1");
     if (o->record_dev && (o->record_every < 1 || o->record_slots < 1))
@@ -1063,7 +1065,7 @@ static ffmin_status minimize_dev(ffmin_system *sys, double *x_dev, const ffmin_o
     const int64_t max_ticks = o->max_ticks > 0 ? o->max_ticks : (int64_t)o->max_evals + 64;
     int64_t ticks = 0;
     bool timeout = false;
-    if (sys->loop_exec) {  // one graph launch runs the whole minimization
+    if (sys->loop_exec && !o->host_loop) {  // one graph launch runs the whole minimization
         sys->h_loop[0] = 0;
         sys->h_loop[1] = max_ticks;
         CK(cudaMemcpyAsync(sys->d_loop, sys->h_loop, 2 * sizeof(int64_t), cudaMemcpyHostToDevice, sys->stream));

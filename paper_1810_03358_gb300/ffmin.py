@@ -51,7 +51,7 @@ class ffmin_options(C.Structure):
                 ("use_learned_precond", C.c_int32), ("max_ticks", C.c_int32),
                 ("record_dev", C.c_void_p), ("record_every", C.c_int32), ("record_slots", C.c_int32),
                 ("fgm_restart", C.c_int32), ("hb_alpha", C.c_double), ("hb_beta", C.c_double),
-                ("gradfree_taylor_r", C.c_double)]
+                ("gradfree_taylor_r", C.c_double), ("host_loop", C.c_int32)]
 
 
 class ffmin_result(C.Structure):

@@ -345,6 +345,25 @@ def test_round_limit_timeout(ff, oracle_mod, method):
         assert method == 1
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_device_loop_equals_host_loop(ff, prec):
+    # the single-launch driver (conditional WHILE node) and the host-replayed
+    # rounds run the same kernels in the same order: identical results,
+    # counts and rounds (batch of 9: the per-system reduction path)
+    systems = [synth.make_system(40 + 23 * k, 360 + k) for k in range(9)]
+    out = []
+    for host_loop in (0, 1):
+        S = ff.System(systems, prec)
+        x = to_dev([s.x for s in systems])
+        r = S.minimize(x, method=3, max_iter=400, host_loop=host_loop)
+        out.append((x.cpu().numpy(), r, S.last_stats()["ticks"]))
+        S.close()
+    (xa, ra, ta), (xb, rb, tb) = out
+    assert np.array_equal(xa, xb)
+    assert ra == rb
+    assert ta == tb
+
+
 def test_already_converged_start(ff, oracle_mod):
     s = synth.make_system(25, 30)
     xo, ro = oracle_mod.minimize(s, s.x, method=3)
