@@ -269,9 +269,11 @@ ffmin_status ffmin_mlp_train(const float *feat_dev, const float *target_dev, int
                              void *cuda_stream);
 int64_t ffmin_mlp_work_floats(void);
 
-/* Autotuner: time the pair kernel (energy + gradient at x_dev) for each
- * candidate work-item layout (3, 6, 10 or 20 (i-tile, j-chunk) items per
- * resident block, which sets the j-chunk length of every system) and keep
+/* Autotuner: for each candidate work-item layout (3, 6, 10 or 20 items per
+ * resident pair-kernel block, which sets the j-chunk length of the row
+ * sweep's (i-tile, j-chunk) items and the number of j-tiles per item of the
+ * symmetric tiles), time the pair kernels at x_dev (one energy + gradient
+ * launch plus three energy-only launches, an L-BFGS step's mix) and keep
  * the fastest; *density_out = the chosen items per block.  The default
  * before any call is 10.  Not in the paper. */
 ffmin_status ffmin_autotune(ffmin_system *sys, const double *x_dev, int32_t *density_out);

@@ -96,9 +96,12 @@ struct ffmin_system {
     Tile *d_tiles = nullptr;
     Item *d_items = nullptr;
     int2 *d_sys_items = nullptr;
-    // symmetric FP64 list (fixed at create)
+    // symmetric list (rebuilt by the autotuner with the same density;
+    // capacities are those of the densest layout)
     int64_t n_slots64 = 0;
-    int n_items64 = 0;
+    int n_items64 = 0, grid_sym = 0;
+    Item *d_items64 = nullptr;
+    int2 *d_sys_items64 = nullptr;
     std::vector<int32_t> term_off[4];  // per-system offsets of bonds, angles, dihedrals, corrections
     int nb_total = 0, na_total = 0, nd_total = 0;
 };
@@ -545,18 +548,24 @@ ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t pre
     for (int b = 0; b < n_sys; b++) sys->sys_natoms[b] = tops[b].n_atoms;
     sys->grid32_max = sys->grid32;
     sys->grid64_max = sys->grid64;
-    // symmetric FP64 list (fixed for the object): about 10 items per
-    // resident FP64 block; it also fills the tiles' row64 / chunk64 / tloc,
-    // which build_items copies
+    // symmetric list: `density` items per resident block of the symmetric
+    // FP64 kernel (the autotuner rebuilds it with the row list); capacity
+    // from the densest layout the autotuner may choose.  It also fills the
+    // tiles' row64 / chunk64 / tloc, which build_items copies
     std::vector<Item> items64;
     std::vector<int2> sys_items64;
     const int grid_sym = pair_grid_size(2);
-    build_items64(sys, 10LL * grid_sym, items64, sys_items64, &sys->n_slots64);
+    sys->grid_sym = grid_sym;
+    int64_t slots_cap = 0;
+    build_items64(sys, (int64_t)AUTOTUNE_DENSITIES[AUTOTUNE_N - 1] * grid_sym, items64, sys_items64, &slots_cap);
+    const size_t items64_cap = items64.size();
+    build_items64(sys, (int64_t)sys->density * grid_sym, items64, sys_items64, &sys->n_slots64);
     sys->n_items64 = (int)items64.size();
-    const bool sym64 = sys->n_slots64 * TI * (int64_t)sizeof(double4_32a) <= SYM64_MAX_BYTES;
+    const bool sym64 = slots_cap * TI * (int64_t)sizeof(double4_32a) <= SYM64_MAX_BYTES;
     if (sym64) sys->grid64_max = grid_sym;
     sys->c.sym64 = sym64 ? 1 : 0;
     sys->c.n_items64 = sym64 ? sys->n_items64 : 0;
+    sys->n_slots64 = slots_cap;  // allocation size of the partial rows
     // capacity: the densest layout the autotuner may choose
     build_items(sys, AUTOTUNE_DENSITIES[AUTOTUNE_N - 1], items, tiles, sys_items);
     sys->items_cap = (int64_t)items.size();
@@ -607,12 +616,12 @@ ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t pre
     c.sys_items = d_sys_items;
     sys->d_sys_items = d_sys_items;
     if (sym64) {
-        Item *d_items64;
-        int2 *d_sys_items64;
-        CKC(upload(sys, &d_items64, items64));
-        CKC(upload(sys, &d_sys_items64, sys_items64));
-        c.items64 = d_items64;
-        c.sys_items64 = d_sys_items64;
+        CKC(dalloc(sys, &sys->d_items64, items64_cap));
+        CKC(cudaMemcpyAsync(sys->d_items64, items64.data(), items64.size() * sizeof(Item), cudaMemcpyHostToDevice,
+                            sys->stream));
+        CKC(upload(sys, &sys->d_sys_items64, sys_items64));
+        c.items64 = sys->d_items64;
+        c.sys_items64 = sys->d_sys_items64;
     }
     CKC(dalloc(sys, &c.act, 2 * (2 * (size_t)n_sys + 2)));
     SysState *d_st;
@@ -1210,8 +1219,20 @@ ffmin_status ffmin_autotune(ffmin_system *sys, const double *x_dev, int32_t *den
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
+    std::vector<Item> items64;
+    std::vector<int2> sys_items64;
     for (int k = 0; k <= AUTOTUNE_N; k++) {
         const int dens = k < AUTOTUNE_N ? AUTOTUNE_DENSITIES[k] : best;
+        if (sys->c.sym64) {  // the symmetric list first: it sets the tiles' row64 / chunk64
+            int64_t slots = 0;
+            build_items64(sys, (int64_t)dens * sys->grid_sym, items64, sys_items64, &slots);
+            CK(cudaMemcpyAsync(sys->d_items64, items64.data(), items64.size() * sizeof(Item),
+                               cudaMemcpyHostToDevice, sys->stream));
+            CK(cudaMemcpyAsync(sys->d_sys_items64, sys_items64.data(), sys_items64.size() * sizeof(int2),
+                               cudaMemcpyHostToDevice, sys->stream));
+            sys->n_items64 = (int)items64.size();
+            sys->c.n_items64 = sys->n_items64;
+        }
         build_items(sys, dens, items, tiles, sys_items);
         CK(cudaMemcpyAsync(sys->d_items, items.data(), items.size() * sizeof(Item), cudaMemcpyHostToDevice,
                            sys->stream));
@@ -1230,16 +1251,23 @@ ffmin_status ffmin_autotune(ffmin_system *sys, const double *x_dev, int32_t *den
         }
         if (k == AUTOTUNE_N) break;  // the best layout is installed
         if ((st = eval_all(sys, x_dev, EV_EG)) != FFMIN_OK) return st;
-        for (int b = 0; b < sys->n_sys; b++) sys->hst[b].ev_kind = EV_EG;
-        if ((st = upload_states(sys)) != FFMIN_OK) return st;
-        if ((st = set_counts(sys)) != FFMIN_OK) return st;
-        CK(launch_pair(sys->c, sys->grid32, sys->grid64, sys->stream));
-        CK(cudaEventRecord(e0, sys->stream));
-        for (int r = 0; r < 3; r++) CK(launch_pair(sys->c, sys->grid32, sys->grid64, sys->stream));
-        CK(cudaEventRecord(e1, sys->stream));
-        CK(cudaEventSynchronize(e1));
+        // score: one E + grad launch and three energy-only launches, the mix
+        // of an L-BFGS step with LS_PAR (the row list serves the FP32 E +
+        // grad, the symmetric list the FP64 terms and every energy-only pass)
         float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, e0, e1));
+        for (int kind : {EV_EG, EV_E}) {
+            for (int b = 0; b < sys->n_sys; b++) sys->hst[b].ev_kind = kind;
+            if ((st = upload_states(sys)) != FFMIN_OK) return st;
+            if ((st = set_counts(sys)) != FFMIN_OK) return st;
+            CK(launch_pair(sys->c, sys->grid32, sys->grid64, sys->stream));
+            CK(cudaEventRecord(e0, sys->stream));
+            for (int r = 0; r < 3; r++) CK(launch_pair(sys->c, sys->grid32, sys->grid64, sys->stream));
+            CK(cudaEventRecord(e1, sys->stream));
+            CK(cudaEventSynchronize(e1));
+            float t = 0.f;
+            CK(cudaEventElapsedTime(&t, e0, e1));
+            ms += kind == EV_EG ? t / 3.f : t;
+        }
         if (k == 0 || ms < best_ms) { best_ms = ms; best = dens; }
     }
     cudaEventDestroy(e0);

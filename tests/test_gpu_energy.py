@@ -139,9 +139,18 @@ def test_autotuned_layout_keeps_parity(ff, oracle_mod, prec):
     d = S.autotune(x)
     assert d in (3, 6, 10, 20)
     e, g = S.energy_grad(x)
+    e_only = S.energy(x)
     g = split(g.cpu().numpy(), systems)
-    S.close()
     for b, s in enumerate(systems):
         dd, st, go = oracle_mod.energy_terms(s, s.x, grad=True)
         assert abs(e[b] - dd["total"]) / dd["sum_abs"] <= TOL[prec]["e"]
+        assert abs(e_only[b] - dd["total"]) / dd["sum_abs"] <= TOL[prec]["e"]
         assert np.abs(g[b] - go).max() / np.abs(go).max() <= TOL[prec]["g"]
+    if prec == 0:  # the retuned lists drive a minimization: the oracle's steps
+        from tests.test_gpu_minimize import prefix_parity
+        kw = dict(method=3, max_iter=40)
+        rg = S.minimize(x, **kw)
+        xg = split(x.cpu().numpy(), systems)
+        for b, s in enumerate(systems):
+            prefix_parity(oracle_mod, s, xg[b], rg[b], kw)
+    S.close()
