@@ -149,6 +149,19 @@ int orc_minimize(int32_t n, orc_fg_fn fg, void *ctx, double *x, const orc_option
 /* Minimize the force field in place (every method, including GRADFREE). */
 int orc_minimize_ff(const orc_ff *ff, double *x, const orc_options *o, orc_result *res);
 
+/* Monotonic basin hopping (the construction of Wales and Doye that Section 2
+ * mentions, monotonic form) on top of the local minimizer of `o`: minimize
+ * from x; then hops times perturb the best point coordinate by coordinate
+ * by step * (2u - 1), u = (SplitMix64(seed, h * n + k) >> 11) * 2^-53,
+ * minimize locally and keep the result when its energy is lower (any
+ * finite result).  x: the kept point on return; res:
+ * its energy, gradient norm and status with iterations and evaluations
+ * summed over all local runs; *accepted: hops kept. */
+int orc_basin_hop(int32_t n, orc_fg_fn fg, void *ctx, double *x, const orc_options *o, int32_t hops,
+                  double step, uint64_t seed, orc_result *res, int32_t *accepted);
+int orc_basin_hop_ff(const orc_ff *ff, double *x, const orc_options *o, int32_t hops, double step,
+                     uint64_t seed, orc_result *res, int32_t *accepted);
+
 /* Optional per-iteration trace of the last orc_minimize* call (f after each
  * accepted step, step length, FGM theta and beta).  Returns entries copied. */
 int32_t orc_trace(double *f, double *h, double *theta, double *beta, int32_t cap);

@@ -864,3 +864,79 @@ int orc_minimize_ff(const orc_ff *ff, double *x, const orc_options *o, orc_resul
     free(n8);
     return st;
 }
+
+/* ---------------- monotonic basin hopping ---------------- */
+/* Perturbation of one coordinate: step * (2u - 1), u = the top 53 bits of
+ * the SplitMix64 output of `seed` at counter `k`, scaled to [0, 1). */
+static double mbh_offset(uint64_t seed, uint64_t k, double step) {
+    const double u = (double)(orc_splitmix64(seed, k) >> 11) * 0x1.0p-53;
+    return step * (2.0 * u - 1.0);
+}
+
+typedef int (*local_fn)(void *ctx, double *x, const orc_options *o, orc_result *r);
+
+/* Monotonic basin hopping on top of a local minimizer (the construction of
+ * Wales and Doye that Section 2 mentions, in its monotonic form): minimize
+ * locally from x; then `hops` times perturb the best point coordinate by
+ * coordinate (x_k + step * (2u - 1), counter hop * n + k), minimize locally
+ * and keep the new point when its energy is lower (any finite result: a
+ * converged run, a capped one, or one whose line search found no further
+ * step).  res: the kept point's energy,
+ * gradient norm and status; iterations and evaluations summed over all
+ * local runs. */
+static int mbh(int32_t n, local_fn local, void *ctx, double *x, const orc_options *o, int32_t hops,
+               double step, uint64_t seed, orc_result *res, int32_t *accepted) {
+    size_t nb = sizeof(double) * (size_t)n;
+    double *best = malloc(nb), *trial = malloc(nb);
+    orc_result r, rb;
+    int32_t acc = 0, it = 0, ne = 0, neg = 0, lsf = 0;
+    local(ctx, x, o, &rb);
+    it += rb.iterations; ne += rb.energy_evals; neg += rb.grad_evals; lsf += rb.ls_failures;
+    memcpy(best, x, nb);
+    for (int32_t h = 0; h < hops; h++) {
+        for (int32_t k = 0; k < n; k++)
+            trial[k] = best[k] + mbh_offset(seed, (uint64_t)h * (uint64_t)n + (uint64_t)k, step);
+        local(ctx, trial, o, &r);
+        it += r.iterations; ne += r.energy_evals; neg += r.grad_evals; lsf += r.ls_failures;
+        const int usable = r.status != ORC_NONFINITE && isfinite(r.energy);
+        if (usable && (!isfinite(rb.energy) || r.energy < rb.energy)) {
+            memcpy(best, trial, nb);
+            rb = r;
+            acc++;
+        }
+    }
+    memcpy(x, best, nb);
+    *res = rb;
+    res->iterations = it;
+    res->energy_evals = ne;
+    res->grad_evals = neg;
+    res->ls_failures = lsf;
+    if (accepted) *accepted = acc;
+    free(best);
+    free(trial);
+    return res->status;
+}
+
+typedef struct {
+    int32_t n;
+    orc_fg_fn fg;
+    void *ctx;
+} fn_ctx_t;
+static int local_fn_generic(void *ctx, double *x, const orc_options *o, orc_result *r) {
+    fn_ctx_t *c = (fn_ctx_t *)ctx;
+    return orc_minimize(c->n, c->fg, c->ctx, x, o, r);
+}
+static int local_fn_ff(void *ctx, double *x, const orc_options *o, orc_result *r) {
+    return orc_minimize_ff((const orc_ff *)ctx, x, o, r);
+}
+
+int orc_basin_hop(int32_t n, orc_fg_fn fg, void *ctx, double *x, const orc_options *o, int32_t hops,
+                  double step, uint64_t seed, orc_result *res, int32_t *accepted) {
+    fn_ctx_t c = {n, fg, ctx};
+    return mbh(n, local_fn_generic, &c, x, o, hops, step, seed, res, accepted);
+}
+
+int orc_basin_hop_ff(const orc_ff *ff, double *x, const orc_options *o, int32_t hops, double step,
+                     uint64_t seed, orc_result *res, int32_t *accepted) {
+    return mbh(3 * ff->n_atoms, local_fn_ff, (void *)ff, x, o, hops, step, seed, res, accepted);
+}

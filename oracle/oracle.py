@@ -91,6 +91,10 @@ def lib():
         L.orc_minimize.argtypes = [C.c_int32, FG_FN, C.c_void_p, _dp, C.POINTER(_Opt),
                                    C.POINTER(_Res)]
         L.orc_minimize_ff.argtypes = [C.POINTER(_FF), _dp, C.POINTER(_Opt), C.POINTER(_Res)]
+        L.orc_basin_hop.argtypes = [C.c_int32, FG_FN, C.c_void_p, _dp, C.POINTER(_Opt), C.c_int32, C.c_double,
+                                    C.c_uint64, C.POINTER(_Res), _ip]
+        L.orc_basin_hop_ff.argtypes = [C.POINTER(_FF), _dp, C.POINTER(_Opt), C.c_int32, C.c_double, C.c_uint64,
+                                       C.POINTER(_Res), _ip]
         L.orc_trace.argtypes = [_dp, _dp, _dp, _dp, C.c_int32]
         L.orc_trace.restype = C.c_int32
         L.orc_lbfgs_direction.argtypes = [C.c_int32, _dp, C.c_int32, _dp, _dp, _dp, _dp]
@@ -270,6 +274,43 @@ def minimize_fn(fg, x0, **kw):
     r = _Res()
     lib().orc_minimize(n, cfun, None, _dptr(xx), C.byref(o), C.byref(r))
     return xx, _result(r)
+
+
+def basin_hop(s, x, hops, step, seed, **kw):
+    """Monotonic basin hopping on the force field; returns (x [N,3], result
+    dict, accepted hops)."""
+    f = _ff(s)
+    xx = _f64(x).reshape(-1).copy()
+    o, keep = options(**kw)
+    r = _Res()
+    acc = C.c_int32()
+    lib().orc_basin_hop_ff(C.byref(f.s), _dptr(xx), C.byref(o), int(hops), float(step), int(seed), C.byref(r),
+                           C.byref(acc))
+    return xx.reshape(-1, 3), _result(r), acc.value
+
+
+def basin_hop_fn(fg, x0, hops, step, seed, **kw):
+    """Monotonic basin hopping on a Python objective (as minimize_fn)."""
+    n = int(np.asarray(x0).size)
+    xx = _f64(x0).reshape(-1).copy()
+
+    def cb(ctx, xp, gp, st):
+        xv = np.ctypeslib.as_array(xp, shape=(n,)).copy()
+        want = bool(gp)
+        f, g = fg(xv, want)
+        if want:
+            ga = np.ctypeslib.as_array(gp, shape=(n,))
+            ga[:] = g
+        st[0] = 0 if np.isfinite(f) else 1
+        return float(f)
+
+    cfun = FG_FN(cb)
+    o, keep = options(**kw)
+    r = _Res()
+    acc = C.c_int32()
+    lib().orc_basin_hop(n, cfun, None, _dptr(xx), C.byref(o), int(hops), float(step), int(seed), C.byref(r),
+                        C.byref(acc))
+    return xx, _result(r), acc.value
 
 
 def trace(cap=200000):
