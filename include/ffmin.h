@@ -236,6 +236,20 @@ ffmin_status ffmin_energy_delta(ffmin_system *sys, const double *x_dev, const do
 ffmin_status ffmin_minimize(ffmin_system *sys, double *x_dev, const ffmin_options *opt,
                             ffmin_result *results);
 
+/* Monotonic basin hopping (the construction of Wales and Doye that Section 2
+ * mentions as a way to deeper minima, in its monotonic form) on top of the
+ * local minimizer of opt, every system of the batch at once: minimize
+ * locally from x_dev; then hops times perturb each system's best point
+ * coordinate by coordinate by step * (2u - 1) (A), u = (SplitMix64(seed + b,
+ * h * 3N_b + k) >> 11) * 2^-53 for coordinate k of system b at hop h,
+ * minimize all systems locally together, and keep each system's new point
+ * when its energy is lower (any finite result).  x_dev (device, in/out):
+ * the kept points; results[b]: the kept point's energy, |grad|_inf and
+ * stop reason, with iterations and evaluations summed over all local runs;
+ * accepted_host[b] (optional): hops kept.  GRADFREE needs one system. */
+ffmin_status ffmin_basin_hop(ffmin_system *sys, double *x_dev, const ffmin_options *opt, int32_t hops,
+                             double step, uint64_t seed, ffmin_result *results, int32_t *accepted_host);
+
 /* Same with a host coordinate buffer (copied in and out). */
 ffmin_status ffmin_minimize_host(ffmin_system *sys, double *x_host, const ffmin_options *opt,
                                  ffmin_result *results);

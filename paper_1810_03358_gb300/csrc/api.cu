@@ -85,6 +85,9 @@ struct ffmin_system {
     bool have_precond = false;
     // some system uses the exclusion variant
     bool has_excl = false;
+    // basin hopping: best points [3N] and per-system accept flags
+    double *mbh_best = nullptr;
+    int32_t *mbh_flags = nullptr;
     // stats of the last minimize
     int64_t last_ticks = 0, last_launches = 0, last_pairs = 0;
     // host copies of the topology needed by the gradient-free path
@@ -1140,6 +1143,74 @@ ffmin_status ffmin_minimize(ffmin_system *sys, double *x_dev, const ffmin_option
     if ((st = check_options(sys, o)) != FFMIN_OK) return st;
     st = minimize_dev(sys, x_dev, o, res);
     if (st != FFMIN_OK) return st;
+    return leave(sys);
+}
+
+ffmin_status ffmin_basin_hop(ffmin_system *sys, double *x_dev, const ffmin_options *o, int32_t hops, double step,
+                             uint64_t seed, ffmin_result *results, int32_t *accepted_host) {
+    NvtxRange nvtx_range("ffmin_basin_hop");
+    ffmin_status st = enter(sys);
+    if (st != FFMIN_OK) return st;
+    if (!x_dev || !results) return fail(sys, FFMIN_ERR_INVALID_ARG, "NULL argument");
+    if (hops < 0 || !(step >= 0.0) || !std::isfinite(step))
+        return fail(sys, FFMIN_ERR_INVALID_ARG, "need hops >= 0 and a finite step >= 0");
+    if ((st = check_options(sys, o)) != FFMIN_OK) return st;
+    const Ctx &c = sys->c;
+    const size_t bytes = sizeof(double) * 3 * sys->n_atoms;
+    if (!sys->mbh_best) {
+        CK(dalloc(sys, &sys->mbh_best, 3 * (size_t)sys->n_atoms));
+        CK(dalloc(sys, &sys->mbh_flags, (size_t)sys->n_sys));
+    }
+    const int n = sys->n_sys;
+    std::vector<ffmin_result> kept(n), cur(n);
+    std::vector<int64_t> tot(4 * (size_t)n, 0);  // iterations, energy / grad evaluations, line-search failures
+    std::vector<int32_t> acc(n, 0), flags(n, 0);
+    int64_t ticks = 0, launches = 0, pairs = 0;
+    auto add = [&](const std::vector<ffmin_result> &r) {
+        for (int b = 0; b < n; b++) {
+            tot[4 * b] += r[b].iterations;
+            tot[4 * b + 1] += r[b].energy_evals;
+            tot[4 * b + 2] += r[b].grad_evals;
+            tot[4 * b + 3] += r[b].ls_failures;
+        }
+        ticks += sys->last_ticks;
+        launches += sys->last_launches;
+        pairs += sys->last_pairs;
+    };
+    // the local minimum of the start
+    if ((st = minimize_dev(sys, x_dev, o, kept.data())) != FFMIN_OK) return st;
+    add(kept);
+    CK(cudaMemcpyAsync(sys->mbh_best, x_dev, bytes, cudaMemcpyDeviceToDevice, sys->stream));
+    for (int32_t h = 0; h < hops; h++) {
+        CK(launch_mbh_perturb(c, sys->mbh_best, x_dev, step, seed, h, sys->stream));
+        if ((st = minimize_dev(sys, x_dev, o, cur.data())) != FFMIN_OK) return st;
+        add(cur);
+        for (int b = 0; b < n; b++) {  // keep any finite lower result
+            const bool usable = cur[b].stop_reason != FFMIN_ERR_NONFINITE && std::isfinite(cur[b].energy);
+            flags[b] = usable && (!std::isfinite(kept[b].energy) || cur[b].energy < kept[b].energy) ? 1 : 0;
+            if (flags[b]) {
+                kept[b] = cur[b];
+                acc[b]++;
+            }
+        }
+        CK(cudaMemcpyAsync(sys->mbh_flags, flags.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice,
+                           sys->stream));
+        CK(launch_mbh_accept(c, sys->mbh_flags, x_dev, sys->mbh_best, sys->stream));
+        CK(cudaStreamSynchronize(sys->stream));  // flags is reused by the next hop
+        launches += 2;
+    }
+    CK(cudaMemcpyAsync(x_dev, sys->mbh_best, bytes, cudaMemcpyDeviceToDevice, sys->stream));
+    for (int b = 0; b < n; b++) {
+        results[b] = kept[b];
+        results[b].iterations = (int32_t)std::min<int64_t>(tot[4 * b], INT32_MAX);
+        results[b].energy_evals = (int32_t)std::min<int64_t>(tot[4 * b + 1], INT32_MAX);
+        results[b].grad_evals = (int32_t)std::min<int64_t>(tot[4 * b + 2], INT32_MAX);
+        results[b].ls_failures = (int32_t)std::min<int64_t>(tot[4 * b + 3], INT32_MAX);
+        if (accepted_host) accepted_host[b] = acc[b];
+    }
+    sys->last_ticks = ticks;
+    sys->last_launches = launches;
+    sys->last_pairs = pairs;
     return leave(sys);
 }
 

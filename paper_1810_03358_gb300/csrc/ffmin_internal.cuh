@@ -203,6 +203,16 @@ struct Ctx {
 
 inline __host__ __device__ double *vslot(const Ctx &c, int slot) { return c.vec + (int64_t)slot * c.vstride; }
 
+// SplitMix64 (Steele, Lea and Flood 2014): the k-th output of the
+// counter-based stream of `seed` (the gradient-free atom picker and the
+// basin-hopping perturbations)
+__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t k) {
+    uint64_t z = seed + (k + 1) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
 // counters[] indices
 enum { CNT_PAIR = 0, CNT_PAIR_EXIT = 1, CNT_FIN = 2, CNT_UPD = 3, CNT_DIR1 = 4, CNT_DIR2 = 5,
        CNT_PARAB = 6, CNT_PARAB2 = 7, CNT_PAIR64 = 8, CNT_PAIR64_EXIT = 9, CNT_N = 10 };
@@ -220,6 +230,12 @@ cudaError_t launch_dir(const Ctx &c, int which, cudaStream_t s);
 // per-system reduction + control step after a stage (only when sep_reduce):
 // stage 0 update, 1 / 2 direction passes, 3 finalize
 cudaError_t launch_sysreduce(const Ctx &c, int stage, cudaStream_t s);
+// basin hopping: out = best + step (2u - 1) per coordinate, u from the
+// SplitMix64 stream of seed + b at counter hop * 3N_b + k (system b); and the
+// copy of x into best for the systems whose flag is set
+cudaError_t launch_mbh_perturb(const Ctx &c, const double *best, double *out, double step, uint64_t seed,
+                               int64_t hop, cudaStream_t s);
+cudaError_t launch_mbh_accept(const Ctx &c, const int32_t *flags, const double *x, double *best, cudaStream_t s);
 // resident blocks of the pair kernel of a mode: 0 FP32 row sweep, 1 FP64
 // row sweep, 2 FP64 symmetric tiles
 int pair_grid_size(int mode);

@@ -432,6 +432,41 @@ cudaError_t launch_ncount(const Ctx &c, const double *x, int32_t *out, cudaStrea
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- basin hopping
+// one block per tile, one thread per atom; the offset is formed as the
+// oracle forms it (this unit has no implicit FMA contraction)
+__global__ void __launch_bounds__(TI) k_mbh_perturb(Ctx c, const double *best, double *out, double step,
+                                                   uint64_t seed, int64_t hop) {
+    const Tile t = c.tiles[blockIdx.x];
+    const int i = threadIdx.x;
+    if (i >= t.na) return;
+    const SysState &S = c.st[t.sys];
+    const int a = t.a0 + i;
+    const uint64_t base = (uint64_t)hop * (uint64_t)(3 * S.natoms) + 3ull * (uint64_t)(a - S.atom0);
+    for (int k = 0; k < 3; k++) {
+        const double u = (double)(splitmix64(seed + (uint64_t)t.sys, base + k) >> 11) * 0x1.0p-53;
+        out[3 * a + k] = best[3 * a + k] + step * (2.0 * u - 1.0);
+    }
+}
+
+__global__ void __launch_bounds__(TI) k_mbh_accept(Ctx c, const int32_t *flags, const double *x, double *best) {
+    const Tile t = c.tiles[blockIdx.x];
+    const int i = threadIdx.x;
+    if (i >= t.na || !flags[t.sys]) return;
+    const int a = t.a0 + i;
+    for (int k = 0; k < 3; k++) best[3 * a + k] = x[3 * a + k];
+}
+
+cudaError_t launch_mbh_perturb(const Ctx &c, const double *best, double *out, double step, uint64_t seed,
+                               int64_t hop, cudaStream_t s) {
+    k_mbh_perturb<<<c.n_tiles, TI, 0, s>>>(c, best, out, step, seed, hop);
+    return cudaGetLastError();
+}
+cudaError_t launch_mbh_accept(const Ctx &c, const int32_t *flags, const double *x, double *best, cudaStream_t s) {
+    k_mbh_accept<<<c.n_tiles, TI, 0, s>>>(c, flags, x, best);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_prepare(const Ctx &c, cudaStream_t s) {
     k_prepare<<<c.n_tiles, TI, 0, s>>>(c);
     return cudaGetLastError();

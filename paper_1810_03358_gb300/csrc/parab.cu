@@ -40,13 +40,6 @@ struct ParabState {
     double p[8][3];
 };
 
-__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t k) {
-    uint64_t z = seed + (k + 1) * 0x9E3779B97F4A7C15ULL;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
-    return z ^ (z >> 31);
-}
-
 __device__ __forceinline__ int pick_atom(uint64_t seed, uint64_t k, int n) {
     return (int)__umul64hi(splitmix64(seed, k), (uint64_t)n);
 }

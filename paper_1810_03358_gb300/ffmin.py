@@ -63,6 +63,7 @@ class ffmin_result(C.Structure):
 EXPORTS = ["ffmin_options_default", "ffmin_status_string", "ffmin_create", "ffmin_destroy",
            "ffmin_n_atoms", "ffmin_atom_offset", "ffmin_energy", "ffmin_energy_grad",
            "ffmin_energy_grad_host", "ffmin_energy_delta", "ffmin_minimize", "ffmin_minimize_host",
+           "ffmin_basin_hop",
            "ffmin_set_precond", "ffmin_time_pair_kernel", "ffmin_last_stats",
            "ffmin_last_error", "ffmin_pair_energy_grad_noalloc", "ffmin_neighbour_counts",
            "ffmin_mlp_train", "ffmin_mlp_work_floats", "ffmin_autotune", "ffmin_alu_peak",
@@ -99,6 +100,8 @@ def lib():
     L.ffmin_energy_delta.argtypes = [vp, vp, vp, C.c_double, _dp]
     L.ffmin_minimize.argtypes = [vp, vp, C.POINTER(ffmin_options), C.POINTER(ffmin_result)]
     L.ffmin_minimize_host.argtypes = [vp, _dp, C.POINTER(ffmin_options), C.POINTER(ffmin_result)]
+    L.ffmin_basin_hop.argtypes = [vp, vp, C.POINTER(ffmin_options), C.c_int32, C.c_double, C.c_uint64,
+                                  C.POINTER(ffmin_result), _ip]
     L.ffmin_set_precond.argtypes = [vp, C.POINTER(C.c_uint16), C.c_int32]
     L.ffmin_time_pair_kernel.argtypes = [vp, vp, C.c_int32, C.c_int32, C.POINTER(C.c_float)]
     L.ffmin_last_stats.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
@@ -265,6 +268,17 @@ def ffmin_minimize(handle, x, options, n_sys=1):
     return _results(rs)
 
 
+def ffmin_basin_hop(handle, x, options, hops, step, seed, n_sys=1):
+    """Monotonic basin hopping in place (x: FP64 CUDA tensor); returns
+    (list of result dicts, list of accepted hops per system)."""
+    rs = (ffmin_result * n_sys)()
+    acc = np.zeros(n_sys, dtype=np.int32)
+    st = lib().ffmin_basin_hop(C.c_void_p(handle), _dev_ptr(x, ffmin_n_atoms(handle)), C.byref(options),
+                               int(hops), float(step), int(seed), rs, acc.ctypes.data_as(_ip))
+    _check(st, handle)
+    return _results(rs), [int(a) for a in acc]
+
+
 def ffmin_minimize_host(handle, x_host, options, n_sys=1):
     """x_host: float64 numpy array [3N], minimized in place."""
     assert x_host.dtype == np.float64 and x_host.flags.c_contiguous
@@ -353,6 +367,10 @@ class System:
     def minimize(self, x, **opts):
         o = ffmin_options_default(**opts)
         return ffmin_minimize(self.handle, x, o, self.n_sys)
+
+    def basin_hop(self, x, hops, step, seed, **opts):
+        o = ffmin_options_default(**opts)
+        return ffmin_basin_hop(self.handle, x, o, hops, step, seed, self.n_sys)
 
     def minimize_host(self, x_host, **opts):
         o = ffmin_options_default(**opts)
