@@ -67,7 +67,7 @@ def test_full_hops_keep_a_valid_lower_minimum(ff, oracle_mod, prec):
     S.close()
     r = res[0]
     assert r["status_name"] == "ok", r
-    assert r["energy"] <= local["energy"] * (1 + 1e-12) if local["energy"] > 0 else r["energy"] <= local["energy"]
+    assert r["energy"] <= local["energy"] + 1e-12 * abs(local["energy"])
     e, g = oracle_mod.energy_grad(s, x.cpu().numpy().reshape(-1, 3))
     assert abs(e - r["energy"]) <= 1e-9 * abs(e)
     assert np.abs(g).max() < 0.1 * (1 + 1e-6)
