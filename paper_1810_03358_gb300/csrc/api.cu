@@ -62,7 +62,7 @@ struct ffmin_system {
     std::vector<int64_t> atom_off;
     std::vector<int32_t> sys_natoms;
     std::vector<SysState> hst;
-    int grid32 = 0, grid64 = 0;
+    int grid32 = 0, grid32e = 0, grid64 = 0;
     int graph_ticks = 0;
     cudaGraphExec_t graph = nullptr;
     int32_t *h_nactive = nullptr;  // pinned
@@ -94,7 +94,7 @@ struct ffmin_system {
     std::vector<int32_t> inc_off_h;
     // work-item layout (rebuilt by the autotuner)
     std::vector<Tile> tiles_h;
-    int n_bitems = 0, n_terms = 0, density = 10, grid32_max = 0, grid64_max = 0;
+    int n_bitems = 0, n_terms = 0, density = 10, grid32_max = 0, grid32e_max = 0, grid64_max = 0;
     int64_t items_cap = 0;
     Tile *d_tiles = nullptr;
     Item *d_items = nullptr;
@@ -236,6 +236,7 @@ static void set_item_counts(ffmin_system *sys, int n_items) {
     // no more resident blocks than work items: idle blocks would only pay
     // for queue atomics
     sys->grid32 = std::max(1, std::min(sys->grid32_max, n_items));
+    sys->grid32e = std::max(1, std::min(sys->grid32e_max, sys->c.sym64 ? sys->n_items64 : n_items));
     sys->grid64 = std::max(1, std::min(sys->grid64_max, sys->c.sym64 ? sys->n_items64 : n_items));
 }
 
@@ -550,6 +551,7 @@ ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t pre
     sys->sys_natoms.resize(n_sys);
     for (int b = 0; b < n_sys; b++) sys->sys_natoms[b] = tops[b].n_atoms;
     sys->grid32_max = sys->grid32;
+    sys->grid32e_max = pair_grid_size(3);
     sys->grid64_max = sys->grid64;
     // symmetric list: `density` items per resident block of the symmetric
     // FP64 kernel (the autotuner rebuilds it with the row list); capacity
@@ -626,7 +628,7 @@ ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t pre
         c.items64 = sys->d_items64;
         c.sys_items64 = sys->d_sys_items64;
     }
-    CKC(dalloc(sys, &c.act, 2 * (2 * (size_t)n_sys + 2)));
+    CKC(dalloc(sys, &c.act, N_LISTS * (2 * (size_t)n_sys + 2)));
     SysState *d_st;
     CKC(dalloc(sys, &d_st, n_sys));
     c.st = d_st;
@@ -780,7 +782,7 @@ static cudaError_t launch_tick(ffmin_system *sys) {
     if ((e = launch_dir(c, 1, s)) != cudaSuccess) return e;
     if (c.sep_reduce && (e = launch_sysreduce(c, 2, s)) != cudaSuccess) return e;
     if ((e = launch_prepare(c, s)) != cudaSuccess) return e;
-    if ((e = launch_pair(c, sys->grid32, sys->grid64, s)) != cudaSuccess) return e;
+    if ((e = launch_pair(c, sys->grid32, sys->grid32e, sys->grid64, s)) != cudaSuccess) return e;
     if ((e = launch_finalize(c, s)) != cudaSuccess) return e;
     if (c.sep_reduce) return launch_sysreduce(c, 3, s);
     return cudaSuccess;
@@ -797,7 +799,7 @@ __global__ void k_loop_cond(cudaGraphConditionalHandle h, const int32_t *nactive
     cudaGraphSetConditional(h, (*nactive > 0 && t < loop[1]) ? 1u : 0u);
 }
 static int kernels_per_tick(const ffmin_system *sys) {
-    return (sys->prec == FFMIN_MIXED ? 7 : 6) + (sys->c.sep_reduce ? 4 : 0);
+    return (sys->prec == FFMIN_MIXED ? 8 : 6) + (sys->c.sep_reduce ? 4 : 0);
 }
 
 static ffmin_status ensure_graph(ffmin_system *sys) {
@@ -885,7 +887,7 @@ static ffmin_status eval_slot(ffmin_system *sys, int slot, int kind, int dir = -
     if (st != FFMIN_OK) return st;
     if ((st = set_counts(sys)) != FFMIN_OK) return st;
     CK(launch_prepare(c, sys->stream));
-    CK(launch_pair(c, sys->grid32, sys->grid64, sys->stream));
+    CK(launch_pair(c, sys->grid32, sys->grid32e, sys->grid64, sys->stream));
     CK(launch_finalize(c, sys->stream));
     if (c.sep_reduce) CK(launch_sysreduce(c, 3, sys->stream));
     return download_states(sys);
@@ -1249,9 +1251,9 @@ ffmin_status ffmin_time_pair_kernel(ffmin_system *sys, const double *x_dev, int3
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    CK(launch_pair(sys->c, sys->grid32, sys->grid64, sys->stream));  // warm-up
+    CK(launch_pair(sys->c, sys->grid32, sys->grid32e, sys->grid64, sys->stream));  // warm-up
     CK(cudaEventRecord(e0, sys->stream));
-    for (int r = 0; r < reps; r++) CK(launch_pair(sys->c, sys->grid32, sys->grid64, sys->stream));
+    for (int r = 0; r < reps; r++) CK(launch_pair(sys->c, sys->grid32, sys->grid32e, sys->grid64, sys->stream));
     CK(cudaEventRecord(e1, sys->stream));
     CK(cudaEventSynchronize(e1));
     float t = 0.f;
@@ -1330,9 +1332,9 @@ ffmin_status ffmin_autotune(ffmin_system *sys, const double *x_dev, int32_t *den
             for (int b = 0; b < sys->n_sys; b++) sys->hst[b].ev_kind = kind;
             if ((st = upload_states(sys)) != FFMIN_OK) return st;
             if ((st = set_counts(sys)) != FFMIN_OK) return st;
-            CK(launch_pair(sys->c, sys->grid32, sys->grid64, sys->stream));
+            CK(launch_pair(sys->c, sys->grid32, sys->grid32e, sys->grid64, sys->stream));
             CK(cudaEventRecord(e0, sys->stream));
-            for (int r = 0; r < 3; r++) CK(launch_pair(sys->c, sys->grid32, sys->grid64, sys->stream));
+            for (int r = 0; r < 3; r++) CK(launch_pair(sys->c, sys->grid32, sys->grid32e, sys->grid64, sys->stream));
             CK(cudaEventRecord(e1, sys->stream));
             CK(cudaEventSynchronize(e1));
             float t = 0.f;

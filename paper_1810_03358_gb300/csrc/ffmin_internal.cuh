@@ -186,8 +186,8 @@ struct Ctx {
     int32_t sym64, n_items64;
     const Item *items64;
     const int2 *sys_items64;
-    int32_t *act;           // per pair-kernel mode m: [m * (2 n_sys + 2)]: active systems, their
-                            // items, item prefix [n_sys], system ids [n_sys] (rebuilt every launch)
+    int32_t *act;           // per work queue L: [L * (2 n_sys + 2)]: active systems, their items,
+                            // item prefix [n_sys], system ids [n_sys] (rebuilt every launch)
     double *te;             // [n_terms] energy of each bonded term
     double *tg;             // [2 nb + 3 na + 4 nd][3] gradient of each term at each position
     // reductions
@@ -215,7 +215,11 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t k) {
 
 // counters[] indices
 enum { CNT_PAIR = 0, CNT_PAIR_EXIT = 1, CNT_FIN = 2, CNT_UPD = 3, CNT_DIR1 = 4, CNT_DIR2 = 5,
-       CNT_PARAB = 6, CNT_PARAB2 = 7, CNT_PAIR64 = 8, CNT_PAIR64_EXIT = 9, CNT_N = 10 };
+       CNT_PARAB = 6, CNT_PARAB2 = 7, CNT_PAIR64 = 8, CNT_PAIR64_EXIT = 9, CNT_PAIR32E = 10, CNT_N = 11 };
+
+// work queues of the pair kernels (one active list each): FP32 E + grad,
+// FP64 terms, FP32 energy only (plain and difference trials)
+enum { LIST_F32_EG = 0, LIST_F64 = 1, LIST_F32_E = 2, N_LISTS = 3 };
 
 // ---- launchers (defined in the .cu files) ----
 cudaError_t launch_prepare(const Ctx &c, cudaStream_t s);
@@ -223,7 +227,7 @@ cudaError_t launch_ncount(const Ctx &c, const double *x, int32_t *out, cudaStrea
 // launches the FP32 kernel (MIXED objects) and the FP64 kernel; each skips
 // the systems of the other precision mode and exits at once when none is
 // in its mode
-cudaError_t launch_pair(const Ctx &c, int grid32, int grid64, cudaStream_t s);
+cudaError_t launch_pair(const Ctx &c, int grid32, int grid32e, int grid64, cudaStream_t s);
 cudaError_t launch_finalize(const Ctx &c, cudaStream_t s);
 cudaError_t launch_update(const Ctx &c, cudaStream_t s);
 cudaError_t launch_dir(const Ctx &c, int which, cudaStream_t s);
@@ -236,8 +240,8 @@ cudaError_t launch_sysreduce(const Ctx &c, int stage, cudaStream_t s);
 cudaError_t launch_mbh_perturb(const Ctx &c, const double *best, double *out, double step, uint64_t seed,
                                int64_t hop, cudaStream_t s);
 cudaError_t launch_mbh_accept(const Ctx &c, const int32_t *flags, const double *x, double *best, cudaStream_t s);
-// resident blocks of the pair kernel of a mode: 0 FP32 row sweep, 1 FP64
-// row sweep, 2 FP64 symmetric tiles
+// resident blocks of the pair kernel of a mode: 0 FP32 E + grad row sweep,
+// 1 FP64 row sweep, 2 FP64 symmetric tiles, 3 FP32 energy only
 int pair_grid_size(int mode);
 
 // arguments of one epoch of the parallel gradient-free search (one block

@@ -239,10 +239,19 @@ __device__ __forceinline__ void sweep_delta_factored(const float4 *__restrict__ 
 // XS: the object carries the exclusion variant (FP32 sweeps scale the listed
 // pairs); a separate instantiation keeps the masked code out of the kernel
 // every other object runs
-template <typename T, int NT, int IPT, bool XS = false>
-__global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? FFMIN_F32_MINBLOCKS : 8)) k_pair(Ctx c);
-template <typename T, int NT, int IPT, bool XS>
-__global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? FFMIN_F32_MINBLOCKS : 8)) k_pair(Ctx c) {
+// EONLY (FP32): the energy-only kernel (plain energies and difference
+// trials, on the symmetric list) with its own work queue; the other FP32
+// instantiation runs the E + grad row sweep only.  The FP64 row sweep (the
+// fallback of batches too large for the symmetric list) takes both kinds.
+#ifndef FFMIN_F32E_MINBLOCKS
+#define FFMIN_F32E_MINBLOCKS FFMIN_F32_MINBLOCKS
+#endif
+template <typename T, int NT, int IPT, bool XS = false, bool EONLY = false>
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? (EONLY ? FFMIN_F32E_MINBLOCKS : FFMIN_F32_MINBLOCKS) : 8))
+    k_pair(Ctx c);
+template <typename T, int NT, int IPT, bool XS, bool EONLY>
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? (EONLY ? FFMIN_F32E_MINBLOCKS : FFMIN_F32_MINBLOCKS) : 8))
+    k_pair(Ctx c) {
     static_assert(NT * IPT == TI, "a block covers one i-tile");
     using V4 = typename VT<T>::V4;
     using V2 = typename VT<T>::V2;
@@ -259,10 +268,11 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? FFMIN_F32_MINBLOCKS : 8)
         pos = c.posd; par = c.pard; out = c.gpd;
     }
     constexpr int MODE = sizeof(T) == 4 ? 0 : 1;
-    constexpr int CNT = MODE == 0 ? CNT_PAIR : CNT_PAIR64;
+    constexpr int LIST = MODE == 1 ? LIST_F64 : (EONLY ? LIST_F32_E : LIST_F32_EG);
+    constexpr int CNT = MODE == 1 ? CNT_PAIR64 : (EONLY ? CNT_PAIR32E : CNT_PAIR);
     // the queue runs over the items of the systems evaluating in this
-    // precision only (active list rebuilt before every launch)
-    const int32_t *A = c.act + MODE * (2 * c.n_sys + 2);
+    // precision and kind only (active list rebuilt before every launch)
+    const int32_t *A = c.act + LIST * (2 * c.n_sys + 2);
     const int n_act = A[0], total = A[1];
     if (total == 0) return;
     const int32_t *aoff = A + 2, *asys = A + 2 + c.n_sys;
@@ -281,7 +291,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? FFMIN_F32_MINBLOCKS : 8)
                 // FP32 energy-only evaluations (plain or difference trials)
                 // run on the symmetric list: each pair once, no forces
                 const int b = asys[lo];
-                const int sym = MODE == 0 && c.sym64 && c.st[b].ev_kind == EV_E;
+                const int sym = MODE == 0 && EONLY && c.sym64;
                 s_item = (sym ? c.sys_items64 : c.sys_items)[b].x + (q - aoff[lo]);
                 s_sym = sym;
             } else {
@@ -301,6 +311,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? FFMIN_F32_MINBLOCKS : 8)
         const Tile tl = c.tiles[I.tile];
         const int kind = c.st[tl.sys].ev_kind;
         if (kind == EV_NONE || c.st[tl.sys].mode != MODE) continue;
+        if (MODE == 0 && (kind == EV_E) != EONLY) continue;  // the other FP32 queue's system
         const bool delta = MODE == 0 && c.st[tl.sys].ev_delta;
         V4 pi[IPT];
         V2 ci[IPT];
@@ -350,7 +361,6 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? FFMIN_F32_MINBLOCKS : 8)
             int dk[IPT];
 #pragma unroll
             for (int u = 0; u < IPT; u++) dk[u] = ig[u] - jt;
-            bool done = false;
             if constexpr (MODE == 0) {
                 // exclusion variant: this j tile holds scaled partners of
                 // the i tile (near the diagonal of a chain); -1 marks padding
@@ -358,34 +368,36 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? FFMIN_F32_MINBLOCKS : 8)
                 int igm[IPT];
 #pragma unroll
                 for (int u = 0; u < IPT; u++) igm[u] = tid + u * NT < tl.na ? ig[u] : -1;
-                if (masked) {
-                    if (delta) {
-                        if (diag && sym) sweep_delta<IPT, 2, true>(sp, sq, sd, pi, ci, di, dk, ec, lj, &c, igm, jt);
-                        else if (diag) sweep_delta<IPT, 1, true>(sp, sq, sd, pi, ci, di, dk, ec, lj, &c, igm, jt);
-                        else sweep_delta<IPT, 0, true>(sp, sq, sd, pi, ci, di, dk, ec, lj, &c, igm, jt);
-                    } else if (kind == EV_EG) {
+                if constexpr (EONLY) {  // energy only: plain or difference trial
+                    if (masked) {
+                        if (delta) {
+                            if (diag && sym) sweep_delta<IPT, 2, true>(sp, sq, sd, pi, ci, di, dk, ec, lj, &c, igm, jt);
+                            else if (diag) sweep_delta<IPT, 1, true>(sp, sq, sd, pi, ci, di, dk, ec, lj, &c, igm, jt);
+                            else sweep_delta<IPT, 0, true>(sp, sq, sd, pi, ci, di, dk, ec, lj, &c, igm, jt);
+                        } else {
+                            if (diag && sym) sweep<T, IPT, false, 2, true>(sp, sq, pi, ci, dk, gx, gy, gz, ec, lj, &c, igm, jt);
+                            else if (diag) sweep<T, IPT, false, 1, true>(sp, sq, pi, ci, dk, gx, gy, gz, ec, lj, &c, igm, jt);
+                            else sweep<T, IPT, false, 0, true>(sp, sq, pi, ci, dk, gx, gy, gz, ec, lj, &c, igm, jt);
+                        }
+                    } else if (delta) {  // factored sums in the (idle) gradient registers
+                        if (diag && sym) sweep_delta_factored<IPT, 2>(sp, sq, sd, pi, di, dk, gx, gy, gz);
+                        else if (diag) sweep_delta_factored<IPT, 1>(sp, sq, sd, pi, di, dk, gx, gy, gz);
+                        else sweep_delta_factored<IPT, 0>(sp, sq, sd, pi, di, dk, gx, gy, gz);
+                    } else {
+                        if (diag && sym) sweep_e_factored<IPT, 2>(sp, sq, pi, dk, gx, gy, gz);
+                        else if (diag) sweep_e_factored<IPT, 1>(sp, sq, pi, dk, gx, gy, gz);
+                        else sweep_e_factored<IPT, 0>(sp, sq, pi, dk, gx, gy, gz);
+                    }
+                } else {  // E + grad row sweep
+                    if (masked) {
                         if (diag) sweep<T, IPT, true, 1, true>(sp, sq, pi, ci, dk, gx, gy, gz, ec, lj, &c, igm, jt);
                         else sweep<T, IPT, true, 0, true>(sp, sq, pi, ci, dk, gx, gy, gz, ec, lj, &c, igm, jt);
                     } else {
-                        if (diag && sym) sweep<T, IPT, false, 2, true>(sp, sq, pi, ci, dk, gx, gy, gz, ec, lj, &c, igm, jt);
-                        else if (diag) sweep<T, IPT, false, 1, true>(sp, sq, pi, ci, dk, gx, gy, gz, ec, lj, &c, igm, jt);
-                        else sweep<T, IPT, false, 0, true>(sp, sq, pi, ci, dk, gx, gy, gz, ec, lj, &c, igm, jt);
+                        if (diag) sweep<T, IPT, true, 1>(sp, sq, pi, ci, dk, gx, gy, gz, ec, lj);
+                        else sweep<T, IPT, true, 0>(sp, sq, pi, ci, dk, gx, gy, gz, ec, lj);
                     }
-                    done = true;
-                } else if (delta) {  // factored sums in the (idle) gradient registers
-                    if (diag && sym) sweep_delta_factored<IPT, 2>(sp, sq, sd, pi, di, dk, gx, gy, gz);
-                    else if (diag) sweep_delta_factored<IPT, 1>(sp, sq, sd, pi, di, dk, gx, gy, gz);
-                    else sweep_delta_factored<IPT, 0>(sp, sq, sd, pi, di, dk, gx, gy, gz);
-                    done = true;
-                } else if (kind == EV_E) {
-                    if (diag && sym) sweep_e_factored<IPT, 2>(sp, sq, pi, dk, gx, gy, gz);
-                    else if (diag) sweep_e_factored<IPT, 1>(sp, sq, pi, dk, gx, gy, gz);
-                    else sweep_e_factored<IPT, 0>(sp, sq, pi, dk, gx, gy, gz);
-                    done = true;
                 }
-            }
-            if (done) {
-            } else if (kind == EV_EG) {
+            } else if (kind == EV_EG) {  // FP64 row sweep (fallback of very large batches)
                 if (diag) sweep<T, IPT, true, 1>(sp, sq, pi, ci, dk, gx, gy, gz, ec, lj);
                 else sweep<T, IPT, true, 0>(sp, sq, pi, ci, dk, gx, gy, gz, ec, lj);
             } else {
@@ -401,7 +413,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? FFMIN_F32_MINBLOCKS : 8)
         }
         // FP32 energy only: masked tiles summed the pair terms into ec / lj,
         // the others the factored sums into gx, gy, gz
-        const bool factored = MODE == 0 && kind == EV_E;
+        constexpr bool factored = MODE == 0 && EONLY;
 #pragma unroll
         for (int u = 0; u < IPT; u++) {
             V4 o;
@@ -570,6 +582,8 @@ __global__ void __launch_bounds__(NT_SYM, 6) k_pair64_sym(Ctx c) {
 constexpr int NT_F32 = TI / FFMIN_F32_IPT, NT_F64 = 128;
 #define K_F32 k_pair<float, NT_F32, FFMIN_F32_IPT>
 #define K_F32X k_pair<float, NT_F32, FFMIN_F32_IPT, true>
+#define K_F32E k_pair<float, NT_F32, FFMIN_F32_IPT, false, true>
+#define K_F32EX k_pair<float, NT_F32, FFMIN_F32_IPT, true, true>
 #define K_F64 k_pair<double, 128, 1>
 
 int pair_grid_size(int mode) {
@@ -580,8 +594,10 @@ int pair_grid_size(int mode) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, K_F32, NT_F32, 0);
     else if (mode == 1)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, K_F64, NT_F64, 0);
-    else
+    else if (mode == 2)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pair64_sym, NT_SYM, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, K_F32E, NT_F32, 0);
     if (per < 1) per = 1;
     return sms * per;
 }
@@ -597,9 +613,10 @@ __global__ void __launch_bounds__(256) k_activelist(Ctx c) {
     if (threadIdx.x == 0) {
         c.counters[CNT_PAIR] = 0;
         c.counters[CNT_PAIR64] = 0;
+        c.counters[CNT_PAIR32E] = 0;
     }
-    for (int m = 0; m < 2; m++) {
-        int32_t *A = c.act + m * (2 * c.n_sys + 2);
+    for (int L = 0; L < N_LISTS; L++) {
+        int32_t *A = c.act + L * (2 * c.n_sys + 2);
         if (threadIdx.x == 0) { base_items = 0; base_sys = 0; }
         __syncthreads();
         for (int b0 = 0; b0 < c.n_sys; b0 += 256) {
@@ -607,10 +624,12 @@ __global__ void __launch_bounds__(256) k_activelist(Ctx c) {
             int n = 0;
             if (b < c.n_sys) {
                 const SysState &S = c.st[b];
-                // FP64 terms and FP32 energy-only evaluations use the
-                // symmetric list (when the object has one)
-                const bool sym = c.sym64 && (m == 1 || S.ev_kind == EV_E);
-                if (S.ev_kind != EV_NONE && S.mode == m) n = (sym ? c.sys_items64 : c.sys_items)[b].y;
+                // queue of the system's evaluation: FP32 E + grad (row list),
+                // FP64 terms or FP32 energy only (symmetric list when the
+                // object has one)
+                const int mine = S.ev_kind == EV_NONE ? -1
+                                 : (S.mode == 1 ? LIST_F64 : (S.ev_kind == EV_E ? LIST_F32_E : LIST_F32_EG));
+                if (mine == L) n = (c.sym64 && L != LIST_F32_EG ? c.sys_items64 : c.sys_items)[b].y;
             }
             const int f = n > 0 ? 1 : 0;
             int si = n, ss = f;  // inclusive scans within the warp
@@ -639,11 +658,16 @@ __global__ void __launch_bounds__(256) k_activelist(Ctx c) {
     }
 }
 
-cudaError_t launch_pair(const Ctx &c, int grid32, int grid64, cudaStream_t s) {
-    k_activelist<<<1, 256, 0, s>>>(c);  // also gives both pair kernels fresh work queues
+cudaError_t launch_pair(const Ctx &c, int grid32, int grid32e, int grid64, cudaStream_t s) {
+    k_activelist<<<1, 256, 0, s>>>(c);  // also gives every pair kernel a fresh work queue
     if (c.prec == FFMIN_MIXED) {
-        if (c.xs_off) K_F32X<<<grid32, NT_F32, 0, s>>>(c);
-        else K_F32<<<grid32, NT_F32, 0, s>>>(c);
+        if (c.xs_off) {
+            K_F32X<<<grid32, NT_F32, 0, s>>>(c);
+            K_F32EX<<<grid32e, NT_F32, 0, s>>>(c);
+        } else {
+            K_F32<<<grid32, NT_F32, 0, s>>>(c);
+            K_F32E<<<grid32e, NT_F32, 0, s>>>(c);
+        }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
