@@ -444,7 +444,11 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? (EONLY ? FFMIN_F32E_MINB
 // kernel sums an atom's j-side rows (tiles I <= its tile) and i-side rows in
 // a fixed order.  Row energies count each pair once.
 constexpr int NT_SYM = 128;
-__global__ void __launch_bounds__(NT_SYM, 6) k_pair64_sym(Ctx c) {
+// resident blocks per SM (6: 80 registers, the FP64 pipe ~90 % busy)
+#ifndef FFMIN_SYM_MINBLOCKS
+#define FFMIN_SYM_MINBLOCKS 6
+#endif
+__global__ void __launch_bounds__(NT_SYM, FFMIN_SYM_MINBLOCKS) k_pair64_sym(Ctx c) {
     __shared__ double4_32a sp[TJ];
     __shared__ double2 sq[TJ];
     __shared__ double jfx[NT_SYM / 32][TJ], jfy[NT_SYM / 32][TJ], jfz[NT_SYM / 32][TJ];
