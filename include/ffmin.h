@@ -178,6 +178,9 @@ typedef struct {
     int32_t grad_evals;      /* energy + gradient evaluations */
     int32_t ls_failures;
     int32_t stop_reason;     /* ffmin_status: OK when converged */
+    int32_t fp64_iterations; /* accepted steps taken with FP64 pair terms: all of
+                                them for FP64, the FP64 phase of a MIXED run
+                                (0 for MIXED gradient-free runs) */
 } ffmin_result;
 
 typedef struct ffmin_system ffmin_system;

@@ -55,6 +55,7 @@ struct ffmin_system {
     cudaStream_t user_stream = nullptr;
     cudaStream_t stream = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    Branches br{};  // side streams of a round's parallel branches
     bool broken = false;
     std::string err;
     Ctx c{};
@@ -208,6 +209,7 @@ static void build_items64(ffmin_system *sys, int64_t want, std::vector<Item> &it
             tl.row64 = (int)items.size();
             tl.chunk64 = chunk;
             tl.tloc = I;
+            tl.slot64 = (int)slots;
             for (int J = I; J < nT; J += chunk) {
                 const int nJ = std::min(chunk, nT - J);
                 const Tile &last = tiles[t0 + J + nJ - 1];
@@ -350,6 +352,11 @@ ffmin_status ffmin_destroy(ffmin_system *sys) {
     if (sys->h_nactive) cudaFreeHost(sys->h_nactive);
     if (sys->ev_in) cudaEventDestroy(sys->ev_in);
     if (sys->ev_out) cudaEventDestroy(sys->ev_out);
+    for (int k = 0; k < 2; k++) {
+        if (sys->br.side[k]) cudaStreamDestroy(sys->br.side[k]);
+        if (sys->br.join[k]) cudaEventDestroy(sys->br.join[k]);
+    }
+    if (sys->br.fork) cudaEventDestroy(sys->br.fork);
     if (sys->stream) cudaStreamDestroy(sys->stream);
     delete sys;
     return FFMIN_OK;
@@ -406,6 +413,16 @@ ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t pre
     if (e != cudaSuccess) { ffmin_status st = cuda_fail(nullptr, e, "cudaStreamCreate"); delete sys; return st; }
     cudaEventCreateWithFlags(&sys->ev_in, cudaEventDisableTiming);
     cudaEventCreateWithFlags(&sys->ev_out, cudaEventDisableTiming);
+    e = cudaEventCreateWithFlags(&sys->br.fork, cudaEventDisableTiming);
+    for (int k = 0; k < 2 && e == cudaSuccess; k++) {
+        e = cudaStreamCreateWithFlags(&sys->br.side[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sys->br.join[k], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        ffmin_status st = cuda_fail(nullptr, e, "side streams");
+        ffmin_destroy(sys);
+        return st;
+    }
     if (cudaMallocHost((void **)&sys->h_nactive, sizeof(int32_t)) != cudaSuccess ||
         cudaMallocHost((void **)&sys->h_loop, 2 * sizeof(int64_t)) != cudaSuccess) {
         ffmin_destroy(sys);
@@ -596,7 +613,7 @@ ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t pre
     c.n_atoms = (int)total;
     c.vstride = ((3 * total + 31) / 32) * 32;
     c.prec = precision;
-    c.sep_reduce = n_sys >= 8 ? 1 : 0;
+    c.sep_reduce = n_sys >= LB_MAX_SYS ? 1 : 0;
 
 #define CKC(call)                                                              \
     do {                                                                       \
@@ -771,6 +788,26 @@ static ffmin_status set_counts(ffmin_system *sys) {
     return FFMIN_OK;
 }
 
+// One evaluation's kernels: the active lists (built from the control state)
+// beside the trial point, then the pair kernels, then the finalize.  The
+// active-list kernel and k_prepare read the same state and write disjoint
+// buffers, so they run on parallel branches.
+static cudaError_t launch_eval(ffmin_system *sys, cudaStream_t s) {
+    const Ctx &c = sys->c;
+    const Branches &br = sys->br;
+    cudaError_t e;
+    if ((e = cudaEventRecord(br.fork, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(br.side[0], br.fork, 0)) != cudaSuccess) return e;
+    if ((e = launch_activelist(c, br.side[0])) != cudaSuccess) return e;
+    if ((e = launch_prepare(c, s)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(br.join[0], br.side[0])) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(s, br.join[0], 0)) != cudaSuccess) return e;
+    if ((e = launch_pair_kernels(c, sys->grid32, sys->grid32e, sys->grid64, s, &br)) != cudaSuccess) return e;
+    if ((e = launch_finalize(c, s)) != cudaSuccess) return e;
+    if (c.sep_reduce) return launch_sysreduce(c, 3, s);
+    return cudaSuccess;
+}
+
 static cudaError_t launch_tick(ffmin_system *sys) {
     const Ctx &c = sys->c;
     cudaStream_t s = sys->stream;
@@ -781,11 +818,7 @@ static cudaError_t launch_tick(ffmin_system *sys) {
     if (c.sep_reduce && (e = launch_sysreduce(c, 1, s)) != cudaSuccess) return e;
     if ((e = launch_dir(c, 1, s)) != cudaSuccess) return e;
     if (c.sep_reduce && (e = launch_sysreduce(c, 2, s)) != cudaSuccess) return e;
-    if ((e = launch_prepare(c, s)) != cudaSuccess) return e;
-    if ((e = launch_pair(c, sys->grid32, sys->grid32e, sys->grid64, s)) != cudaSuccess) return e;
-    if ((e = launch_finalize(c, s)) != cudaSuccess) return e;
-    if (c.sep_reduce) return launch_sysreduce(c, 3, s);
-    return cudaSuccess;
+    return launch_eval(sys, s);
 }
 
 constexpr int TICKS_PER_GRAPH = 8;
@@ -886,10 +919,7 @@ static ffmin_status eval_slot(ffmin_system *sys, int slot, int kind, int dir = -
     ffmin_status st = upload_states(sys);
     if (st != FFMIN_OK) return st;
     if ((st = set_counts(sys)) != FFMIN_OK) return st;
-    CK(launch_prepare(c, sys->stream));
-    CK(launch_pair(c, sys->grid32, sys->grid32e, sys->grid64, sys->stream));
-    CK(launch_finalize(c, sys->stream));
-    if (c.sep_reduce) CK(launch_sysreduce(c, 3, sys->stream));
+    CK(launch_eval(sys, sys->stream));
     return download_states(sys);
 }
 
@@ -1125,6 +1155,7 @@ static ffmin_status minimize_dev(ffmin_system *sys, double *x_dev, const ffmin_o
         r.grad_evals = S.neg;
         r.ls_failures = S.lsf;
         r.stop_reason = (timeout && S.active) ? FFMIN_ERR_TIMEOUT : S.status;
+        r.fp64_iterations = S.mode == 1 ? S.iter - S.iter_fp64_0 : 0;
         if (timeout && S.active) {  // still running: the last accepted (FGM: best) point
             const bool fgm = S.method == FFMIN_FGM;
             r.energy = fgm ? S.fb : S.f;
@@ -1165,15 +1196,16 @@ ffmin_status ffmin_basin_hop(ffmin_system *sys, double *x_dev, const ffmin_optio
     }
     const int n = sys->n_sys;
     std::vector<ffmin_result> kept(n), cur(n);
-    std::vector<int64_t> tot(4 * (size_t)n, 0);  // iterations, energy / grad evaluations, line-search failures
+    std::vector<int64_t> tot(5 * (size_t)n, 0);  // iterations, energy / grad evaluations, line-search failures, FP64 steps
     std::vector<int32_t> acc(n, 0), flags(n, 0);
     int64_t ticks = 0, launches = 0, pairs = 0;
     auto add = [&](const std::vector<ffmin_result> &r) {
         for (int b = 0; b < n; b++) {
-            tot[4 * b] += r[b].iterations;
-            tot[4 * b + 1] += r[b].energy_evals;
-            tot[4 * b + 2] += r[b].grad_evals;
-            tot[4 * b + 3] += r[b].ls_failures;
+            tot[5 * b] += r[b].iterations;
+            tot[5 * b + 1] += r[b].energy_evals;
+            tot[5 * b + 2] += r[b].grad_evals;
+            tot[5 * b + 3] += r[b].ls_failures;
+            tot[5 * b + 4] += r[b].fp64_iterations;
         }
         ticks += sys->last_ticks;
         launches += sys->last_launches;
@@ -1204,10 +1236,11 @@ ffmin_status ffmin_basin_hop(ffmin_system *sys, double *x_dev, const ffmin_optio
     CK(cudaMemcpyAsync(x_dev, sys->mbh_best, bytes, cudaMemcpyDeviceToDevice, sys->stream));
     for (int b = 0; b < n; b++) {
         results[b] = kept[b];
-        results[b].iterations = (int32_t)std::min<int64_t>(tot[4 * b], INT32_MAX);
-        results[b].energy_evals = (int32_t)std::min<int64_t>(tot[4 * b + 1], INT32_MAX);
-        results[b].grad_evals = (int32_t)std::min<int64_t>(tot[4 * b + 2], INT32_MAX);
-        results[b].ls_failures = (int32_t)std::min<int64_t>(tot[4 * b + 3], INT32_MAX);
+        results[b].iterations = (int32_t)std::min<int64_t>(tot[5 * b], INT32_MAX);
+        results[b].energy_evals = (int32_t)std::min<int64_t>(tot[5 * b + 1], INT32_MAX);
+        results[b].grad_evals = (int32_t)std::min<int64_t>(tot[5 * b + 2], INT32_MAX);
+        results[b].ls_failures = (int32_t)std::min<int64_t>(tot[5 * b + 3], INT32_MAX);
+        results[b].fp64_iterations = (int32_t)std::min<int64_t>(tot[5 * b + 4], INT32_MAX);
         if (accepted_host) accepted_host[b] = acc[b];
     }
     sys->last_ticks = ticks;
@@ -1447,6 +1480,7 @@ static ffmin_status parab_minimize(ffmin_system *sys, const ffmin_options *o, ff
     res[0].grad_evals = neg;
     res[0].ls_failures = 0;
     res[0].stop_reason = status;
+    res[0].fp64_iterations = sys->prec == FFMIN_MIXED ? 0 : moves;
     sys->last_ticks = ticks;
     sys->last_launches = launches;
     sys->last_pairs = (int64_t)moves * 8 * (n - 1) + (int64_t)neg * n * (int64_t)(n - 1) / 2;
@@ -1634,6 +1668,7 @@ static ffmin_status epoch_minimize(ffmin_system *sys, const ffmin_options *o, ff
     res[0].grad_evals = neg;
     res[0].ls_failures = 0;
     res[0].stop_reason = status;
+    res[0].fp64_iterations = sys->prec == FFMIN_MIXED ? 0 : moves;
     sys->last_ticks = ticks;
     sys->last_launches = launches;
     sys->last_pairs = (int64_t)moves * 8 * (n - 1) + (int64_t)neg * n * (int64_t)(n - 1) / 2;

@@ -71,6 +71,7 @@ __device__ void finish(const Ctx &c, SysState &S, int status, double res_f, doub
     if (S.mixed && S.mode == 0 && S.phase != PH_EVAL_ONLY &&
         (status == FFMIN_OK || status == FFMIN_ERR_LINESEARCH)) {
         S.mode = 1;
+        S.iter_fp64_0 = S.iter;
         atomicSub(&c.nmode[0], 1);
         atomicAdd(&c.nmode[1], 1);
         S.dir[0].on = 0;

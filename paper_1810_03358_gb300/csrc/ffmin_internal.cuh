@@ -67,9 +67,12 @@ constexpr int BONDED_ITEM_TERMS = 64;
 // item0 / nitem: the tile's items in the row-sweep list; row64: its first
 // item in the symmetric list (row of tile pairs (tile, J >= tile)), chunk64:
 // j-tiles per symmetric item of its system, tloc: index inside its system;
+// slot64: the partial-row slot of its row's first symmetric item (the row's
+// items hold consecutive slots, 1 + chunk64 per item, so the q-th item of
+// the row starts at slot64 + q * (1 + chunk64));
 // xlo / xhi: the smallest and largest scaled partner (exclusion variant) of
 // its atoms, xlo > xhi when there is none
-struct Tile { int32_t sys, a0, na, item0, nitem, row64, chunk64, tloc, xlo, xhi, pad0, pad1; };
+struct Tile { int32_t sys, a0, na, item0, nitem, row64, chunk64, tloc, xlo, xhi, slot64, pad1; };
 
 struct DirOp {
     int32_t on, use_d, dots;  // dots: 1 -> |R|^2, <G,R>; 2 -> <Y_j, R> for the Y list
@@ -129,6 +132,7 @@ struct SysState {
     // precision: mixed = 1 for a MIXED object; mode 0 = FP32 pair terms,
     // mode 1 = FP64 pair terms (the FP64 phase of a mixed run, or always)
     int32_t mixed, mode, stall;
+    int32_t iter_fp64_0;  // S.iter when the FP64 phase began (0: FP64 throughout)
     double f32_best;
     // preconditioner: 1 when the current direction used the learned diagonal
     int32_t dir_used_d, rec_every;
@@ -140,6 +144,11 @@ struct SysState {
 // below this multiple of the tolerance (the FP64 phase then certifies the
 // point); a failed FP32 line search also hands over
 constexpr double MIXED_SWITCH_RATIO = 1.0;
+
+// batches of at least this many systems reduce and run their control steps
+// in k_sysreduce (one block per system); smaller ones in the last block of
+// each per-tile kernel
+constexpr int LB_MAX_SYS = 8;
 
 struct Ctx {
     int32_t n_sys, n_tiles, n_items, n_atoms;
@@ -228,6 +237,17 @@ cudaError_t launch_ncount(const Ctx &c, const double *x, int32_t *out, cudaStrea
 // the systems of the other precision mode and exits at once when none is
 // in its mode
 cudaError_t launch_pair(const Ctx &c, int grid32, int grid32e, int grid64, cudaStream_t s);
+// side streams and events for parallel branches of one round: work forked
+// from the main stream (event fork) and joined back (events join[k])
+struct Branches {
+    cudaStream_t side[2];
+    cudaEvent_t fork, join[2];
+};
+cudaError_t launch_activelist(const Ctx &c, cudaStream_t s);
+// the pair kernels alone (launch_pair = active lists, then these in turn);
+// with br, the FP32 energy-only and FP64 kernels run on br's side streams
+cudaError_t launch_pair_kernels(const Ctx &c, int grid32, int grid32e, int grid64, cudaStream_t s,
+                                const Branches *br);
 cudaError_t launch_finalize(const Ctx &c, cudaStream_t s);
 cudaError_t launch_update(const Ctx &c, cudaStream_t s);
 cudaError_t launch_dir(const Ctx &c, int which, cudaStream_t s);

@@ -65,6 +65,37 @@ __global__ void __launch_bounds__(TI) k_prepare(Ctx c) {
 }
 
 // ---------------------------------------------------------------- finalize
+// sum over q < n of f(q) (a double4; only .x .y .z when XYZ, only .w when
+// W) in four interleaved strands (q mod 4), combined as (s0 + s1) + (s2 + s3):
+// every group of four loads is issued together and no dependent chain of
+// FP64 adds is longer than n / 4 + 2
+template <bool XYZ, bool W, typename F>
+__device__ __forceinline__ double4 strand_sum(int n, F f) {
+    double ax[4] = {0.0, 0.0, 0.0, 0.0}, ay[4] = {0.0, 0.0, 0.0, 0.0};
+    double az[4] = {0.0, 0.0, 0.0, 0.0}, aw[4] = {0.0, 0.0, 0.0, 0.0};
+    int q = 0;
+    for (; q + 4 <= n; q += 4) {
+        double4 p[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) p[u] = f(q + u);
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            if (XYZ) { ax[u] += p[u].x; ay[u] += p[u].y; az[u] += p[u].z; }
+            if (W) aw[u] += p[u].w;
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 3; u++) {
+        if (q + u < n) {
+            const double4 p = f(q + u);
+            if (XYZ) { ax[u] += p.x; ay[u] += p.y; az[u] += p.z; }
+            if (W) aw[u] += p.w;
+        }
+    }
+    return make_double4(XYZ ? (ax[0] + ax[1]) + (ax[2] + ax[3]) : 0.0, XYZ ? (ay[0] + ay[1]) + (ay[2] + ay[3]) : 0.0,
+                        XYZ ? (az[0] + az[1]) + (az[2] + az[3]) : 0.0, W ? (aw[0] + aw[1]) + (aw[2] + aw[3]) : 0.0);
+}
+
 __global__ void __launch_bounds__(TI) k_finalize(Ctx c) {
     const Tile t = c.tiles[blockIdx.x];
     const int kind = c.st[t.sys].ev_kind;
@@ -75,62 +106,89 @@ __global__ void __launch_bounds__(TI) k_finalize(Ctx c) {
     const int i = threadIdx.x;
     if (kind != EV_NONE && i < t.na) {
         const int a = t.a0 + i;
-        double e = 0.0, g0 = 0.0, g1 = 0.0, g2 = 0.0;
+        double e, g0 = 0.0, g1 = 0.0, g2 = 0.0;
         if (mode == 0 && c.sym64 && kind == EV_E) {
             // FP32 energy only on the symmetric list: the i-side rows of the
-            // tile's own row of items, each pair counted once
+            // tile's own row of items (consecutive slots, 1 + C apart), each
+            // pair counted once
             const SysState &S = c.st[t.sys];
             const int T = t.tloc, C = t.chunk64;
             const int nch = (S.ntile - T + C - 1) / C;
-            for (int q = 0; q < nch; q++) e += (double)c.gpf_sym[(int64_t)c.items64[t.row64 + q].slot * TI + i].w;
+            e = strand_sum<false, true>(nch, [&](int q) {
+                    const float4 p = c.gpf_sym[((int64_t)t.slot64 + (int64_t)q * (1 + C)) * TI + i];
+                    return make_double4(0.0, 0.0, 0.0, (double)p.w);
+                }).w;
         } else if (mode == 0) {
-            for (int it = 0; it < t.nitem; it++) {
+            const double4 r = strand_sum<true, true>(t.nitem, [&](int it) {
                 const float4 p = c.gpf[(int64_t)(t.item0 + it) * TI + i];
-                e += (double)p.w;
-                g0 += (double)p.x; g1 += (double)p.y; g2 += (double)p.z;
-            }
-            e = 0.5 * e;  // every pair was counted in both of its rows
+                return make_double4((double)p.x, (double)p.y, (double)p.z, (double)p.w);
+            });
+            e = 0.5 * r.w;  // every pair was counted in both of its rows
+            g0 = r.x; g1 = r.y; g2 = r.z;
         } else if (c.sym64) {
             // symmetric tiles: the j-side rows this tile received from the
-            // items of rows I <= T (in I order), then its own row's i-side
-            // rows; each pair's energy was counted once
+            // items of rows I <= T, then its own row's i-side rows; each
+            // pair's energy was counted once (the slot of row I's item u is
+            // tiles[I].slot64 + u * (1 + C))
             const SysState &S = c.st[t.sys];
             const int T = t.tloc, C = t.chunk64;
-            if (kind == EV_EG) {
-                for (int I = 0; I <= T; I++) {
+            double4 rj = make_double4(0.0, 0.0, 0.0, 0.0);
+            if (kind == EV_EG)
+                rj = strand_sum<true, false>(T + 1, [&](int I) {
                     const int q = T - I;
-                    const int slot = c.items64[c.tiles[S.tile0 + I].row64 + q / C].slot + 1 + q % C;
-                    const double4_32a p = c.gpd[(int64_t)slot * TI + i];
-                    g0 += p.x; g1 += p.y; g2 += p.z;
-                }
-            }
+                    const int64_t slot = (int64_t)c.tiles[S.tile0 + I].slot64 + (int64_t)(q / C) * (1 + C) + 1 + q % C;
+                    const double4_32a p = c.gpd[slot * TI + i];
+                    return make_double4(p.x, p.y, p.z, 0.0);
+                });
             const int nch = (S.ntile - T + C - 1) / C;
-            for (int q = 0; q < nch; q++) {
-                const double4_32a p = c.gpd[(int64_t)c.items64[t.row64 + q].slot * TI + i];
-                e += p.w;
-                g0 += p.x; g1 += p.y; g2 += p.z;
-            }
+            const double4 ri = strand_sum<true, true>(nch, [&](int q) {
+                const double4_32a p = c.gpd[((int64_t)t.slot64 + (int64_t)q * (1 + C)) * TI + i];
+                return make_double4(p.x, p.y, p.z, p.w);
+            });
+            e = ri.w;
+            g0 = rj.x + ri.x; g1 = rj.y + ri.y; g2 = rj.z + ri.z;
         } else {
-            for (int it = 0; it < t.nitem; it++) {
+            const double4 r = strand_sum<true, true>(t.nitem, [&](int it) {
                 const double4_32a p = c.gpd[(int64_t)(t.item0 + it) * TI + i];
-                e += p.w;
-                g0 += p.x; g1 += p.y; g2 += p.z;
-            }
-            e = 0.5 * e;  // every pair was counted in both of its rows
+                return make_double4(p.x, p.y, p.z, p.w);
+            });
+            e = 0.5 * r.w;  // every pair was counted in both of its rows
+            g0 = r.x; g1 = r.y; g2 = r.z;
         }
         v[RF_EPAIR] = e;
         // bonded terms: evaluated once per term by the pair kernel's bonded
         // items; every atom gathers its terms' energies (as owner) and
-        // position gradients through its incidence list
+        // position gradients through its incidence list (four entries'
+        // loads issued together; entry u of each group to strand u mod 2)
         const bool grad = kind == EV_EG;
-        for (int k = c.inc_off[a]; k < c.inc_off[a + 1]; k++) {
-            const int2 in = c.inc[k];
-            const int type = in.x >> 2, pos = in.x & 3;
-            if (pos == 0) e += c.te[bonded_index(c, type, in.y)];
-            if (grad) {
-                const double *gb = c.tg + 3 * bonded_grad_slot(c, type, in.y, pos);
-                g0 += gb[0]; g1 += gb[1]; g2 += gb[2];
+        double be[2] = {0.0, 0.0}, bg[2][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+        const int k1 = c.inc_off[a + 1];
+        for (int k = c.inc_off[a]; k < k1; k += 4) {
+            int2 in[4];
+            double te[4], gb[4][3];
+#pragma unroll
+            for (int u = 0; u < 4; u++) in[u] = k + u < k1 ? c.inc[k + u] : make_int2(-1, 0);
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int type = in[u].x >> 2, pos = in[u].x & 3;
+                te[u] = in[u].x >= 0 && pos == 0 ? c.te[bonded_index(c, type, in[u].y)] : 0.0;
+                if (grad && in[u].x >= 0) {
+                    const double *g = c.tg + 3 * bonded_grad_slot(c, type, in[u].y, pos);
+                    gb[u][0] = g[0]; gb[u][1] = g[1]; gb[u][2] = g[2];
+                }
             }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                if (in[u].x < 0) break;
+                if ((in[u].x & 3) == 0) be[u & 1] += te[u];
+                if (grad) { bg[u & 1][0] += gb[u][0]; bg[u & 1][1] += gb[u][1]; bg[u & 1][2] += gb[u][2]; }
+            }
+        }
+        e += be[0] + be[1];
+        if (grad) {
+            g0 += bg[0][0] + bg[1][0];
+            g1 += bg[0][1] + bg[1][1];
+            g2 += bg[0][2] + bg[1][2];
         }
         v[RF_E] = e;
         bool bad = !isfinite(e);
@@ -387,18 +445,24 @@ __global__ void __launch_bounds__(TI) k_sysreduce(Ctx c) {
         maxmask = (1u << RF_GINF) | (1u << RF_BAD);
     }
     __shared__ double tot[NRED];
+    __shared__ SysState sS;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int k = w; k < nv; k += NW) {
         const double x = warp_sys_sum(c, S, k, (maxmask >> k) & 1u);
         if (lane == 0) tot[k] = x;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        if (STAGE == 0) on_update_done(c, S, tot);
-        else if (STAGE == 1) on_dir_done(c, S, 0, tot);
-        else if (STAGE == 2) on_dir_done(c, S, 1, tot);
-        else on_eval_done(c, S, tot);
+    if (w != 0) return;
+    // the control step on a shared-memory copy of the state
+    warp_copy_state(&sS, &S);
+    if (lane == 0) {
+        if (STAGE == 0) on_update_done(c, sS, tot);
+        else if (STAGE == 1) on_dir_done(c, sS, 0, tot);
+        else if (STAGE == 2) on_dir_done(c, sS, 1, tot);
+        else on_eval_done(c, sS, tot);
     }
+    __syncwarp();
+    warp_copy_state(&S, &sS);
 }
 
 cudaError_t launch_sysreduce(const Ctx &c, int stage, cudaStream_t s) {

@@ -444,9 +444,10 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? (EONLY ? FFMIN_F32E_MINB
 // kernel sums an atom's j-side rows (tiles I <= its tile) and i-side rows in
 // a fixed order.  Row energies count each pair once.
 constexpr int NT_SYM = 128;
-// resident blocks per SM (6: 80 registers, the FP64 pipe ~90 % busy)
+// resident blocks per SM: 7 caps the kernel at 72 registers (a few spilled
+// stack bytes) and measured 1.5 % faster than 6 (80 registers, no spills)
 #ifndef FFMIN_SYM_MINBLOCKS
-#define FFMIN_SYM_MINBLOCKS 6
+#define FFMIN_SYM_MINBLOCKS 7
 #endif
 __global__ void __launch_bounds__(NT_SYM, FFMIN_SYM_MINBLOCKS) k_pair64_sym(Ctx c) {
     __shared__ double4_32a sp[TJ];
@@ -662,22 +663,53 @@ __global__ void __launch_bounds__(256) k_activelist(Ctx c) {
     }
 }
 
-cudaError_t launch_pair(const Ctx &c, int grid32, int grid32e, int grid64, cudaStream_t s) {
+cudaError_t launch_activelist(const Ctx &c, cudaStream_t s) {
     k_activelist<<<1, 256, 0, s>>>(c);  // also gives every pair kernel a fresh work queue
-    if (c.prec == FFMIN_MIXED) {
-        if (c.xs_off) {
-            K_F32X<<<grid32, NT_F32, 0, s>>>(c);
-            K_F32EX<<<grid32e, NT_F32, 0, s>>>(c);
-        } else {
-            K_F32<<<grid32, NT_F32, 0, s>>>(c);
-            K_F32E<<<grid32e, NT_F32, 0, s>>>(c);
-        }
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    if (c.sym64) k_pair64_sym<<<grid64, NT_SYM, 0, s>>>(c);
-    else K_F64<<<grid64, NT_F64, 0, s>>>(c);
     return cudaGetLastError();
+}
+
+// The three pair kernels of a MIXED object take disjoint work queues and
+// write disjoint outputs, so with side streams the FP32 energy-only and the
+// FP64 kernels run beside the FP32 E + grad kernel (parallel graph branches
+// when captured): a round waits for the slowest, not for all three in turn.
+cudaError_t launch_pair_kernels(const Ctx &c, int grid32, int grid32e, int grid64, cudaStream_t s,
+                                const Branches *br) {
+    cudaError_t e;
+    if (c.prec != FFMIN_MIXED) {
+        if (c.sym64) k_pair64_sym<<<grid64, NT_SYM, 0, s>>>(c);
+        else K_F64<<<grid64, NT_F64, 0, s>>>(c);
+        return cudaGetLastError();
+    }
+    cudaStream_t se = s, s64 = s;
+    if (br) {
+        if ((e = cudaEventRecord(br->fork, s)) != cudaSuccess) return e;
+        for (int k = 0; k < 2; k++)
+            if ((e = cudaStreamWaitEvent(br->side[k], br->fork, 0)) != cudaSuccess) return e;
+        se = br->side[0];
+        s64 = br->side[1];
+    }
+    if (c.xs_off) {
+        K_F32X<<<grid32, NT_F32, 0, s>>>(c);
+        K_F32EX<<<grid32e, NT_F32, 0, se>>>(c);
+    } else {
+        K_F32<<<grid32, NT_F32, 0, s>>>(c);
+        K_F32E<<<grid32e, NT_F32, 0, se>>>(c);
+    }
+    if (c.sym64) k_pair64_sym<<<grid64, NT_SYM, 0, s64>>>(c);
+    else K_F64<<<grid64, NT_F64, 0, s64>>>(c);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (br) {
+        for (int k = 0; k < 2; k++) {
+            if ((e = cudaEventRecord(br->join[k], br->side[k])) != cudaSuccess) return e;
+            if ((e = cudaStreamWaitEvent(s, br->join[k], 0)) != cudaSuccess) return e;
+        }
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_pair(const Ctx &c, int grid32, int grid32e, int grid64, cudaStream_t s) {
+    cudaError_t e = launch_activelist(c, s);
+    return e != cudaSuccess ? e : launch_pair_kernels(c, grid32, grid32e, grid64, s, nullptr);
 }
 
 }  // namespace ffm

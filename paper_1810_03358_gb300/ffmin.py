@@ -57,7 +57,8 @@ class ffmin_options(C.Structure):
 class ffmin_result(C.Structure):
     _fields_ = [("energy", C.c_double), ("grad_inf", C.c_double), ("iterations", C.c_int32),
                 ("energy_evals", C.c_int32), ("grad_evals", C.c_int32),
-                ("ls_failures", C.c_int32), ("stop_reason", C.c_int32)]
+                ("ls_failures", C.c_int32), ("stop_reason", C.c_int32),
+                ("fp64_iterations", C.c_int32)]
 
 
 EXPORTS = ["ffmin_options_default", "ffmin_status_string", "ffmin_create", "ffmin_destroy",

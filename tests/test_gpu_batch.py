@@ -90,6 +90,7 @@ def test_batch_lbfgs_prefix_fp64(ff, oracle_mod, n_sys, cap):
     ref = oracle_map(_oracle_minimize, systems, [s.x for s in systems], [kw] * n_sys)
     for b, s in enumerate(systems):
         prefix_parity(oracle_mod, s, xg[b], rg[b], kw, ref=ref[b])
+        assert rg[b]["fp64_iterations"] == rg[b]["iterations"], b  # FP64 pair terms throughout
 
 
 def test_batch_other_methods_prefix_fp64(ff, oracle_mod):
@@ -122,3 +123,5 @@ def test_batch_mixed_minimization_certified(ff, oracle_mod):
         assert rg[b]["status_name"] == "ok", (b, rg[b])
         assert np.abs(go).max() < 0.1 * (1 + 1e-6), b
         assert abs(d["total"] - rg[b]["energy"]) <= 1e-9 * abs(d["total"]), b
+        assert 0 <= rg[b]["fp64_iterations"] <= rg[b]["iterations"], b  # the FP64 phase's share
+    print("FP64-phase steps per system:", [r["fp64_iterations"] for r in rg])
