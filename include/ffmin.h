@@ -168,6 +168,14 @@ typedef struct {
      * systems after each replay: the same work and results, for profilers
      * that cannot look into conditional graph nodes. */
     int32_t host_loop;
+    /* L-BFGS with the learned diagonal (not in the paper): every pc_window
+     * accepted steps (default 200; 0: never) the run compares E with its
+     * value pc_window steps earlier; if it fell by less than pc_rel |E|
+     * (default 1e-5) while |grad E|_inf > pc_gfar * gtol_inf (default 100),
+     * the rest of the run is plain L-BFGS (an energy stalled far from a
+     * stationary point).  The FP64 phase of a MIXED run starts a new count. */
+    int32_t pc_window;
+    double pc_rel, pc_gfar;
 } ffmin_options;
 
 typedef struct {
@@ -289,11 +297,23 @@ int64_t ffmin_mlp_work_floats(void);
 /* Autotuner: for each candidate work-item layout (3, 6, 10 or 20 items per
  * resident pair-kernel block, which sets the j-chunk length of the row
  * sweep's (i-tile, j-chunk) items and the number of j-tiles per item of the
- * symmetric tiles), time the pair kernels at x_dev (one energy + gradient
- * launch plus three energy-only launches, an L-BFGS step's mix) and keep
- * the fastest; *density_out = the chosen items per block.  The default
- * before any call is 10.  Not in the paper. */
+ * symmetric tiles) and, for MIXED objects, each FP32 pair-kernel tile shape
+ * (two i-atoms per thread in 64-thread blocks, or one in 128-thread
+ * blocks), time the pair kernels at x_dev (one energy + gradient launch
+ * plus three energy-only launches, an L-BFGS step's mix) and keep the
+ * fastest; *density_out = the chosen items per block (ffmin_get_tuning
+ * reports the shape too).  The defaults before any call are 10 items per
+ * block and two i-atoms per thread.  Synchronizes.  Not in the paper. */
 ffmin_status ffmin_autotune(ffmin_system *sys, const double *x_dev, int32_t *density_out);
+
+/* Install a layout without timing (e.g. one an earlier ffmin_autotune chose
+ * for the same batch): density in [1, 20] items per resident block,
+ * f32_atoms_per_thread 1 or 2 (the FP32 tile shape; FP64 objects ignore
+ * it).  Results do not depend on either, up to the rounding of the FP32
+ * partial sums.  INVALID_ARG otherwise.  Synchronizes. */
+ffmin_status ffmin_set_tuning(ffmin_system *sys, int32_t density, int32_t f32_atoms_per_thread);
+/* The installed layout: items per resident block and FP32 i-atoms per thread. */
+ffmin_status ffmin_get_tuning(const ffmin_system *sys, int32_t *density, int32_t *f32_atoms_per_thread);
 
 /* Time the dominant pair kernel alone: reps launches at x_dev with forces
  * (with_grad = 1), energy only (0), or as a MIXED line-search difference

@@ -133,6 +133,12 @@ typedef struct {
     double hb_alpha, hb_beta;  /* heavy ball (Eq. 8): constant step alpha > 0 and momentum beta >= 0 */
     int32_t fgm_restart;       /* FGM: 1 adds the function-value momentum restart (not in Algorithm 1) */
     double fgm_step;           /* FGM: fixed step 1/L instead of the line search when > 0 (tests) */
+    /* L-BFGS with mlp_w (not in the paper): every pc_window accepted steps
+     * (0: never) E is compared with its value at the last check (first: the
+     * start); if it fell by less than pc_rel |E| while |grad|_inf >
+     * pc_gfar * gtol_inf, the rest of the run is plain L-BFGS */
+    int32_t pc_window;
+    double pc_rel, pc_gfar;
 } orc_options;
 
 typedef struct {

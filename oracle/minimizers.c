@@ -103,6 +103,9 @@ void orc_options_default(orc_options *o) {
     o->gradfree_delta = 0.05;
     o->seed = 12345;
     o->precond_d = NULL;
+    o->pc_window = 200;
+    o->pc_rel = 1e-5;
+    o->pc_gfar = 100.0;
 }
 
 static double finite_or_inf(double f) { return isfinite(f) ? f : HUGE_VAL; }
@@ -529,9 +532,12 @@ int orc_minimize(int32_t n, orc_fg_fn fg, void *ctx, double *x, const orc_option
     /* GD, CG, L-BFGS */
     if (ginf < op->gtol_inf) goto done;
     for (int32_t k = 0; k < n; k++) r[k] = -g[k];
+    int pc_on = g_diag != NULL; /* learned diagonal in use, and its safeguard's mark */
+    int32_t pc_it = it;
+    double pc_f = f;
     for (;;) {
         if (CAP_HIT(it, o)) { status = ORC_MAX_ITER; break; }
-        if (method == ORC_LBFGS && g_diag && hist > 0) {
+        if (method == ORC_LBFGS && g_diag && pc_on && hist > 0) {
             /* learned diagonal; plain L-BFGS when it gives no descent direction */
             orc_precond_diag(g_diag->ff, g_diag->w, g_diag->n8, g, xt);
             orc_lbfgs_direction(n, g, hist, S, Y, xt, r);
@@ -596,6 +602,12 @@ int orc_minimize(int32_t n, orc_fg_fn fg, void *ctx, double *x, const orc_option
         f = fn;
         ginf = gninf;
         if (ginf < op->gtol_inf) { status = ORC_OK; break; }
+        if (pc_on && op->pc_window > 0 && it - pc_it >= op->pc_window) {
+            /* the energy stalled far from a stationary point: plain L-BFGS */
+            if (ginf > op->pc_gfar * op->gtol_inf && !(pc_f - f >= op->pc_rel * fabs(pc_f))) pc_on = 0;
+            pc_it = it;
+            pc_f = f;
+        }
     }
     result_f = f;
     result_ginf = ginf;

@@ -49,7 +49,8 @@ class _Opt(C.Structure):
                 ("gradfree_delta", C.c_double), ("seed", C.c_uint64), ("gradfree_parts", C.c_int32),
                 ("gradfree_margin", C.c_double), ("gradfree_taylor_r", C.c_double), ("precond_d", _dp),
                 ("mlp_w", _dp), ("ogm_step", C.c_double), ("hb_alpha", C.c_double),
-                ("hb_beta", C.c_double), ("fgm_restart", C.c_int32), ("fgm_step", C.c_double)]
+                ("hb_beta", C.c_double), ("fgm_restart", C.c_int32), ("fgm_step", C.c_double),
+                ("pc_window", C.c_int32), ("pc_rel", C.c_double), ("pc_gfar", C.c_double)]
 
 
 class _Res(C.Structure):

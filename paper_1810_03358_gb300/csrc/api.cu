@@ -96,6 +96,7 @@ struct ffmin_system {
     // work-item layout (rebuilt by the autotuner)
     std::vector<Tile> tiles_h;
     int n_bitems = 0, n_terms = 0, density = 10, grid32_max = 0, grid32e_max = 0, grid64_max = 0;
+    int grid32_max_s[2] = {0, 0}, grid32e_max_s[2] = {0, 0};  // per FP32 shape (1 or 2 i-atoms per thread)
     int64_t items_cap = 0;
     Tile *d_tiles = nullptr;
     Item *d_items = nullptr;
@@ -314,6 +315,9 @@ void ffmin_options_default(ffmin_options *o) {
     o->hb_beta = 0.5;
     o->gradfree_taylor_r = 0.0;
     o->host_loop = 0;
+    o->pc_window = 200;
+    o->pc_rel = 1e-5;
+    o->pc_gfar = 100.0;
 }
 
 const char *ffmin_status_string(ffmin_status s) {
@@ -567,8 +571,15 @@ ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t pre
     std::vector<int2> sys_items;
     sys->sys_natoms.resize(n_sys);
     for (int b = 0; b < n_sys; b++) sys->sys_natoms[b] = tops[b].n_atoms;
-    sys->grid32_max = sys->grid32;
-    sys->grid32e_max = pair_grid_size(3);
+    for (int k = 0; k < 2; k++) {
+        sys->grid32_max_s[k] = pair_grid_size(0, k + 1);
+        sys->grid32e_max_s[k] = pair_grid_size(3, k + 1);
+    }
+    sys->c.f32_ipt = 2;
+    // the row list's capacity below takes the FP32 shape with more
+    // resident blocks (more items at a given density)
+    sys->grid32_max = std::max(sys->grid32_max_s[0], sys->grid32_max_s[1]);
+    sys->grid32e_max = sys->grid32e_max_s[1];
     sys->grid64_max = sys->grid64;
     // symmetric list: `density` items per resident block of the symmetric
     // FP64 kernel (the autotuner rebuilds it with the row list); capacity
@@ -591,6 +602,7 @@ ffmin_status ffmin_create(const ffmin_topology *tops, int32_t n_sys, int32_t pre
     // capacity: the densest layout the autotuner may choose
     build_items(sys, AUTOTUNE_DENSITIES[AUTOTUNE_N - 1], items, tiles, sys_items);
     sys->items_cap = (int64_t)items.size();
+    sys->grid32_max = sys->grid32_max_s[1];
     build_items(sys, sys->density, items, tiles, sys_items);
     std::vector<int32_t> inc_off(total + 1, 0);
     std::vector<int2> inc;
@@ -1040,6 +1052,8 @@ static ffmin_status check_options(ffmin_system *sys, const ffmin_options *o) {
     if (o->use_learned_precond && !sys->have_precond)
         return fail(sys, FFMIN_ERR_INVALID_ARG, "no preconditioner weights set");
     if (o->host_loop != 0 && o->host_loop != 1) return fail(sys, FFMIN_ERR_INVALID_ARG, "host_loop must be 0 or 1");
+    if (o->pc_window < 0 || !(o->pc_rel >= 0.0) || !(o->pc_gfar >= 0.0))
+        return fail(sys, FFMIN_ERR_INVALID_ARG, "pc_window >= 0, pc_rel >= 0, pc_gfar >= 0");
     if (o->fgm_restart != 0 && o->fgm_restart != 1)
         return fail(sys, FFMIN_ERR_INVALID_ARG, "fgm_restart must be 0 or 1");
     if (o->record_dev && (o->record_every < 1 || o->record_slots < 1))
@@ -1089,8 +1103,11 @@ static ffmin_status minimize_dev(ffmin_system *sys, double *x_dev, const ffmin_o
         S.rec_slots = o->record_dev ? o->record_slots : 0;
         S.mixed = sys->prec == FFMIN_MIXED ? 1 : 0;
         S.mode = S.mixed ? 0 : 1;
-        S.f32_best = HUGE_VAL;
-        S.stall = 0;
+        S.pc_window = o->pc_window;
+        S.pc_rel = o->pc_rel;
+        S.pc_gfar = o->pc_gfar;
+        S.pc_mark_iter = 0;
+        S.pc_mark_f = 0.0;
         S.active = 1;
         S.phase = PH_START;
         S.result_slot = o->method == FFMIN_FGM ? V_XB : V_X;
@@ -1312,77 +1329,110 @@ ffmin_status ffmin_neighbour_counts(ffmin_system *sys, const double *x_dev, int3
     return leave(sys);
 }
 
+// Installs the work-item layout of a density (both lists, the tiles' list
+// fields, grid sizes) and the FP32 kernel shape; the captured graphs are
+// rebuilt at the next minimization.
+static ffmin_status install_layout(ffmin_system *sys, int dens, int ipt) {
+    sys->c.f32_ipt = ipt;
+    sys->grid32_max = sys->grid32_max_s[ipt - 1];
+    sys->grid32e_max = sys->grid32e_max_s[ipt - 1];
+    std::vector<Item> items, items64;
+    std::vector<Tile> tiles;
+    std::vector<int2> sys_items, sys_items64;
+    if (sys->c.sym64) {  // the symmetric list first: it sets the tiles' row64 / chunk64 / slot64
+        int64_t slots = 0;
+        build_items64(sys, (int64_t)dens * sys->grid_sym, items64, sys_items64, &slots);
+        CK(cudaMemcpyAsync(sys->d_items64, items64.data(), items64.size() * sizeof(Item), cudaMemcpyHostToDevice,
+                           sys->stream));
+        CK(cudaMemcpyAsync(sys->d_sys_items64, sys_items64.data(), sys_items64.size() * sizeof(int2),
+                           cudaMemcpyHostToDevice, sys->stream));
+        sys->n_items64 = (int)items64.size();
+        sys->c.n_items64 = sys->n_items64;
+    }
+    build_items(sys, dens, items, tiles, sys_items);
+    CK(cudaMemcpyAsync(sys->d_items, items.data(), items.size() * sizeof(Item), cudaMemcpyHostToDevice,
+                       sys->stream));
+    CK(cudaMemcpyAsync(sys->d_sys_items, sys_items.data(), sys_items.size() * sizeof(int2), cudaMemcpyHostToDevice,
+                       sys->stream));
+    CK(cudaMemcpyAsync(sys->d_tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice,
+                       sys->stream));
+    set_item_counts(sys, (int)items.size());
+    sys->density = dens;
+    if (sys->graph) {  // kernel parameters (item count, grid, shape) changed
+        cudaGraphExecDestroy(sys->graph);
+        sys->graph = nullptr;
+    }
+    if (sys->loop_exec) {
+        cudaGraphExecDestroy(sys->loop_exec);
+        sys->loop_exec = nullptr;
+    }
+    return FFMIN_OK;
+}
+
 ffmin_status ffmin_autotune(ffmin_system *sys, const double *x_dev, int32_t *density_out) {
     NvtxRange nvtx_range("ffmin_autotune");
     ffmin_status st = enter(sys);
     if (st != FFMIN_OK) return st;
     if (!x_dev) return fail(sys, FFMIN_ERR_INVALID_ARG, "NULL argument");
-    std::vector<Item> items;
-    std::vector<Tile> tiles;
-    std::vector<int2> sys_items;
     float best_ms = 0.f;
-    int best = sys->density;
+    int best = sys->density, best_ipt = sys->c.f32_ipt;
+    bool have = false;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    std::vector<Item> items64;
-    std::vector<int2> sys_items64;
-    for (int k = 0; k <= AUTOTUNE_N; k++) {
-        const int dens = k < AUTOTUNE_N ? AUTOTUNE_DENSITIES[k] : best;
-        if (sys->c.sym64) {  // the symmetric list first: it sets the tiles' row64 / chunk64
-            int64_t slots = 0;
-            build_items64(sys, (int64_t)dens * sys->grid_sym, items64, sys_items64, &slots);
-            CK(cudaMemcpyAsync(sys->d_items64, items64.data(), items64.size() * sizeof(Item),
-                               cudaMemcpyHostToDevice, sys->stream));
-            CK(cudaMemcpyAsync(sys->d_sys_items64, sys_items64.data(), sys_items64.size() * sizeof(int2),
-                               cudaMemcpyHostToDevice, sys->stream));
-            sys->n_items64 = (int)items64.size();
-            sys->c.n_items64 = sys->n_items64;
+    // FP32 shapes: both for MIXED objects, whose FP32 kernels do the work
+    const int n_shapes = sys->prec == FFMIN_MIXED ? 2 : 1;
+    for (int sh = 0; sh < n_shapes; sh++) {
+        const int ipt = 2 - sh;
+        for (int k = 0; k < AUTOTUNE_N; k++) {
+            const int dens = AUTOTUNE_DENSITIES[k];
+            if ((st = install_layout(sys, dens, ipt)) != FFMIN_OK) return st;
+            if ((st = eval_all(sys, x_dev, EV_EG)) != FFMIN_OK) return st;
+            // score: one E + grad launch and three energy-only launches, the
+            // mix of an L-BFGS step with LS_PAR (the row list serves the FP32
+            // E + grad, the symmetric list the FP64 terms and every
+            // energy-only pass)
+            float ms = 0.f;
+            for (int kind : {EV_EG, EV_E}) {
+                for (int b = 0; b < sys->n_sys; b++) sys->hst[b].ev_kind = kind;
+                if ((st = upload_states(sys)) != FFMIN_OK) return st;
+                if ((st = set_counts(sys)) != FFMIN_OK) return st;
+                CK(launch_pair(sys->c, sys->grid32, sys->grid32e, sys->grid64, sys->stream));
+                CK(cudaEventRecord(e0, sys->stream));
+                for (int r = 0; r < 3; r++) CK(launch_pair(sys->c, sys->grid32, sys->grid32e, sys->grid64, sys->stream));
+                CK(cudaEventRecord(e1, sys->stream));
+                CK(cudaEventSynchronize(e1));
+                float t = 0.f;
+                CK(cudaEventElapsedTime(&t, e0, e1));
+                ms += kind == EV_EG ? t / 3.f : t;
+            }
+            if (!have || ms < best_ms) { best_ms = ms; best = dens; best_ipt = ipt; have = true; }
         }
-        build_items(sys, dens, items, tiles, sys_items);
-        CK(cudaMemcpyAsync(sys->d_items, items.data(), items.size() * sizeof(Item), cudaMemcpyHostToDevice,
-                           sys->stream));
-        CK(cudaMemcpyAsync(sys->d_sys_items, sys_items.data(), sys_items.size() * sizeof(int2),
-                           cudaMemcpyHostToDevice, sys->stream));
-        CK(cudaMemcpyAsync(sys->d_tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice,
-                           sys->stream));
-        set_item_counts(sys, (int)items.size());
-        if (sys->graph) {  // kernel parameters (item count, grid) changed
-            cudaGraphExecDestroy(sys->graph);
-            sys->graph = nullptr;
-        }
-        if (sys->loop_exec) {
-            cudaGraphExecDestroy(sys->loop_exec);
-            sys->loop_exec = nullptr;
-        }
-        if (k == AUTOTUNE_N) break;  // the best layout is installed
-        if ((st = eval_all(sys, x_dev, EV_EG)) != FFMIN_OK) return st;
-        // score: one E + grad launch and three energy-only launches, the mix
-        // of an L-BFGS step with LS_PAR (the row list serves the FP32 E +
-        // grad, the symmetric list the FP64 terms and every energy-only pass)
-        float ms = 0.f;
-        for (int kind : {EV_EG, EV_E}) {
-            for (int b = 0; b < sys->n_sys; b++) sys->hst[b].ev_kind = kind;
-            if ((st = upload_states(sys)) != FFMIN_OK) return st;
-            if ((st = set_counts(sys)) != FFMIN_OK) return st;
-            CK(launch_pair(sys->c, sys->grid32, sys->grid32e, sys->grid64, sys->stream));
-            CK(cudaEventRecord(e0, sys->stream));
-            for (int r = 0; r < 3; r++) CK(launch_pair(sys->c, sys->grid32, sys->grid32e, sys->grid64, sys->stream));
-            CK(cudaEventRecord(e1, sys->stream));
-            CK(cudaEventSynchronize(e1));
-            float t = 0.f;
-            CK(cudaEventElapsedTime(&t, e0, e1));
-            ms += kind == EV_EG ? t / 3.f : t;
-        }
-        if (k == 0 || ms < best_ms) { best_ms = ms; best = dens; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    sys->density = best;
+    if ((st = install_layout(sys, best, best_ipt)) != FFMIN_OK) return st;
     for (int b = 0; b < sys->n_sys; b++) sys->hst[b].ev_kind = EV_NONE;
     if ((st = upload_states(sys)) != FFMIN_OK) return st;
     if (density_out) *density_out = best;
     return leave(sys);
+}
+
+ffmin_status ffmin_set_tuning(ffmin_system *sys, int32_t density, int32_t f32_atoms_per_thread) {
+    ffmin_status st = enter(sys);
+    if (st != FFMIN_OK) return st;
+    if (density < 1 || density > AUTOTUNE_DENSITIES[AUTOTUNE_N - 1] ||
+        (f32_atoms_per_thread != 1 && f32_atoms_per_thread != 2))
+        return fail(sys, FFMIN_ERR_INVALID_ARG, "density in [1, 20], f32_atoms_per_thread 1 or 2");
+    if ((st = install_layout(sys, density, f32_atoms_per_thread)) != FFMIN_OK) return st;
+    return leave(sys);
+}
+
+ffmin_status ffmin_get_tuning(const ffmin_system *sys, int32_t *density, int32_t *f32_atoms_per_thread) {
+    if (!sys) return FFMIN_ERR_INVALID_ARG;
+    if (density) *density = sys->density;
+    if (f32_atoms_per_thread) *f32_atoms_per_thread = sys->c.f32_ipt;
+    return FFMIN_OK;
 }
 
 ffmin_status ffmin_last_stats(const ffmin_system *sys, int64_t *ticks, int64_t *launches, int64_t *pairs) {

@@ -467,6 +467,8 @@ __device__ void on_eval_done(const Ctx &c, SysState &S, const double *v) {
         }
         S.result_slot = V_X;
         S.f = E;
+        S.pc_mark_iter = S.iter;  // the learned-diagonal safeguard's first mark
+        S.pc_mark_f = E;
         S.gg = v[RF_GG];
         S.ginf = v[RF_GINF];
         S.upd.op = U_ACCEPT;
@@ -721,6 +723,14 @@ __device__ void on_update_done(const Ctx &c, SysState &S, const double *v) {
     if (S.ginf < S.gtol || mixed_handover(S, S.f, S.ginf)) {
         finish(c, S, FFMIN_OK, S.f, S.ginf);
         return;
+    }
+    // learned-diagonal safeguard (not in the paper): a run whose energy
+    // stalls far from a stationary point with the diagonal continues as
+    // plain L-BFGS, the method's own fallback
+    if (S.precond_on && S.pc_window > 0 && S.iter - S.pc_mark_iter >= S.pc_window) {
+        if (S.ginf > S.pc_gfar * S.gtol && !(S.pc_mark_f - S.f >= S.pc_rel * fabs(S.pc_mark_f))) S.precond_on = 0;
+        S.pc_mark_iter = S.iter;
+        S.pc_mark_f = S.f;
     }
     const int n = S.ring_count;
     if (n == 0) {

@@ -131,9 +131,13 @@ struct SysState {
     int32_t precond_on;
     // precision: mixed = 1 for a MIXED object; mode 0 = FP32 pair terms,
     // mode 1 = FP64 pair terms (the FP64 phase of a mixed run, or always)
-    int32_t mixed, mode, stall;
+    int32_t mixed, mode;
     int32_t iter_fp64_0;  // S.iter when the FP64 phase began (0: FP64 throughout)
-    double f32_best;
+    // learned-diagonal safeguard: every pc_window accepted steps with the
+    // diagonal, E must have fallen by pc_rel |E| since the mark (pc_mark_*)
+    // while |grad|_inf > pc_gfar * gtol, else the run continues without it
+    int32_t pc_window, pc_mark_iter;
+    double pc_rel, pc_gfar, pc_mark_f;
     // preconditioner: 1 when the current direction used the learned diagonal
     int32_t dir_used_d, rec_every;
     int32_t rec_slots, rec_pad;
@@ -155,6 +159,7 @@ struct Ctx {
     int64_t vstride;
     int32_t prec;           // ffmin_precision
     int32_t sep_reduce;     // 1: per-system reductions + control in separate kernels (large batches)
+    int32_t f32_ipt;        // FP32 pair-kernel shape: i-atoms per thread (1 or 2; host-side dispatch)
     const Tile *tiles;
     const Item *items;
     SysState *st;
@@ -262,7 +267,7 @@ cudaError_t launch_mbh_perturb(const Ctx &c, const double *best, double *out, do
 cudaError_t launch_mbh_accept(const Ctx &c, const int32_t *flags, const double *x, double *best, cudaStream_t s);
 // resident blocks of the pair kernel of a mode: 0 FP32 E + grad row sweep,
 // 1 FP64 row sweep, 2 FP64 symmetric tiles, 3 FP32 energy only
-int pair_grid_size(int mode);
+int pair_grid_size(int mode, int f32_ipt = 2);
 
 // arguments of one epoch of the parallel gradient-free search (one block
 // per part, each on its own copy of the positions)

@@ -224,17 +224,17 @@ __device__ __forceinline__ void sweep_delta_factored(const float4 *__restrict__ 
 }
 
 // NT threads per block, IPT i-atoms per thread, NT * IPT == TI (one tile).
-// Register caps: the FP32 kernel (2 i-atoms per thread) runs at 12 resident
-// 64-thread blocks per SM (80 registers; measured on GB300 faster than 16
-// blocks at 64 registers and than 4 i-atoms per thread), the FP64 kernel at
-// 8 blocks of 128 (64 registers); the rarely-run bonded items may spill.
-// FFMIN_F32_IPT / FFMIN_F32_MINBLOCKS override the FP32 shape (the register
-// cap follows: 65536 / (blocks * threads)).
-#ifndef FFMIN_F32_IPT
-#define FFMIN_F32_IPT 2
-#endif
-#ifndef FFMIN_F32_MINBLOCKS
-#define FFMIN_F32_MINBLOCKS (768 / TI * FFMIN_F32_IPT)
+// FP32 shapes: two i-atoms per thread (64-thread blocks: every j load from
+// shared memory serves two pairs) or one (128-thread blocks: twice the warps
+// per work item, which pays when an object has few items); the autotuner
+// picks one per object.  Register caps: FP32 kernels run 768 threads per SM
+// (12 blocks of 64 or 6 of 128, 80 registers; measured on GB300 faster than
+// 1,024 threads at 64 registers and than 4 i-atoms per thread), the FP64
+// kernel 8 blocks of 128 (64 registers); the rarely-run bonded items may
+// spill.  FFMIN_F32_THREADS_PER_SM overrides the FP32 cap (registers per
+// thread follow: 65536 / threads).
+#ifndef FFMIN_F32_THREADS_PER_SM
+#define FFMIN_F32_THREADS_PER_SM 768
 #endif
 // XS: the object carries the exclusion variant (FP32 sweeps scale the listed
 // pairs); a separate instantiation keeps the masked code out of the kernel
@@ -243,15 +243,10 @@ __device__ __forceinline__ void sweep_delta_factored(const float4 *__restrict__ 
 // trials, on the symmetric list) with its own work queue; the other FP32
 // instantiation runs the E + grad row sweep only.  The FP64 row sweep (the
 // fallback of batches too large for the symmetric list) takes both kinds.
-#ifndef FFMIN_F32E_MINBLOCKS
-#define FFMIN_F32E_MINBLOCKS FFMIN_F32_MINBLOCKS
-#endif
 template <typename T, int NT, int IPT, bool XS = false, bool EONLY = false>
-__global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? (EONLY ? FFMIN_F32E_MINBLOCKS : FFMIN_F32_MINBLOCKS) : 8))
-    k_pair(Ctx c);
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? FFMIN_F32_THREADS_PER_SM / NT : 8)) k_pair(Ctx c);
 template <typename T, int NT, int IPT, bool XS, bool EONLY>
-__global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? (EONLY ? FFMIN_F32E_MINBLOCKS : FFMIN_F32_MINBLOCKS) : 8))
-    k_pair(Ctx c) {
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? FFMIN_F32_THREADS_PER_SM / NT : 8)) k_pair(Ctx c) {
     static_assert(NT * IPT == TI, "a block covers one i-tile");
     using V4 = typename VT<T>::V4;
     using V2 = typename VT<T>::V2;
@@ -582,29 +577,43 @@ __global__ void __launch_bounds__(NT_SYM, FFMIN_SYM_MINBLOCKS) k_pair64_sym(Ctx 
     }
 }
 
-// launch shapes: FP32 two i-atoms per thread (halves shared-memory loads
-// per pair), FP64 one (the FP64 pipe, not the loads, is the limit)
-constexpr int NT_F32 = TI / FFMIN_F32_IPT, NT_F64 = 128;
-#define K_F32 k_pair<float, NT_F32, FFMIN_F32_IPT>
-#define K_F32X k_pair<float, NT_F32, FFMIN_F32_IPT, true>
-#define K_F32E k_pair<float, NT_F32, FFMIN_F32_IPT, false, true>
-#define K_F32EX k_pair<float, NT_F32, FFMIN_F32_IPT, true, true>
+// FP64 row sweep: one i-atom per thread (the FP64 pipe, not the loads, is
+// the limit)
+constexpr int NT_F64 = 128;
 #define K_F64 k_pair<double, 128, 1>
 
-int pair_grid_size(int mode) {
+int pair_grid_size(int mode, int f32_ipt) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (mode == 0)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, K_F32, NT_F32, 0);
+    const bool one = f32_ipt == 1;
+    if (mode == 0 && one)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pair<float, TI, 1>, TI, 0);
+    else if (mode == 0)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pair<float, TI / 2, 2>, TI / 2, 0);
     else if (mode == 1)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, K_F64, NT_F64, 0);
     else if (mode == 2)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pair64_sym, NT_SYM, 0);
+    else if (one)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pair<float, TI, 1, false, true>, TI, 0);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, K_F32E, NT_F32, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pair<float, TI / 2, 2, false, true>, TI / 2, 0);
     if (per < 1) per = 1;
     return sms * per;
+}
+
+// the FP32 E + grad and energy-only kernels of one shape
+template <int IPT>
+static void launch_f32(const Ctx &c, int grid32, int grid32e, cudaStream_t s, cudaStream_t se) {
+    constexpr int NT = TI / IPT;
+    if (c.xs_off) {
+        k_pair<float, NT, IPT, true><<<grid32, NT, 0, s>>>(c);
+        k_pair<float, NT, IPT, true, true><<<grid32e, NT, 0, se>>>(c);
+    } else {
+        k_pair<float, NT, IPT><<<grid32, NT, 0, s>>>(c);
+        k_pair<float, NT, IPT, false, true><<<grid32e, NT, 0, se>>>(c);
+    }
 }
 
 // Active lists for the two pair kernels: for each precision mode, the
@@ -688,13 +697,8 @@ cudaError_t launch_pair_kernels(const Ctx &c, int grid32, int grid32e, int grid6
         se = br->side[0];
         s64 = br->side[1];
     }
-    if (c.xs_off) {
-        K_F32X<<<grid32, NT_F32, 0, s>>>(c);
-        K_F32EX<<<grid32e, NT_F32, 0, se>>>(c);
-    } else {
-        K_F32<<<grid32, NT_F32, 0, s>>>(c);
-        K_F32E<<<grid32e, NT_F32, 0, se>>>(c);
-    }
+    if (c.f32_ipt == 1) launch_f32<1>(c, grid32, grid32e, s, se);
+    else launch_f32<2>(c, grid32, grid32e, s, se);
     if (c.sym64) k_pair64_sym<<<grid64, NT_SYM, 0, s64>>>(c);
     else K_F64<<<grid64, NT_F64, 0, s64>>>(c);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

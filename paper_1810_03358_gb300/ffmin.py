@@ -51,7 +51,8 @@ class ffmin_options(C.Structure):
                 ("use_learned_precond", C.c_int32), ("max_ticks", C.c_int32),
                 ("record_dev", C.c_void_p), ("record_every", C.c_int32), ("record_slots", C.c_int32),
                 ("fgm_restart", C.c_int32), ("hb_alpha", C.c_double), ("hb_beta", C.c_double),
-                ("gradfree_taylor_r", C.c_double), ("host_loop", C.c_int32)]
+                ("gradfree_taylor_r", C.c_double), ("host_loop", C.c_int32),
+                ("pc_window", C.c_int32), ("pc_rel", C.c_double), ("pc_gfar", C.c_double)]
 
 
 class ffmin_result(C.Structure):
@@ -67,7 +68,8 @@ EXPORTS = ["ffmin_options_default", "ffmin_status_string", "ffmin_create", "ffmi
            "ffmin_basin_hop",
            "ffmin_set_precond", "ffmin_time_pair_kernel", "ffmin_last_stats",
            "ffmin_last_error", "ffmin_pair_energy_grad_noalloc", "ffmin_neighbour_counts",
-           "ffmin_mlp_train", "ffmin_mlp_work_floats", "ffmin_autotune", "ffmin_alu_peak",
+           "ffmin_mlp_train", "ffmin_mlp_work_floats", "ffmin_autotune", "ffmin_set_tuning",
+           "ffmin_get_tuning", "ffmin_alu_peak",
            "ffmin_epoch_parts"]
 
 _lib = None
@@ -109,6 +111,8 @@ def lib():
     L.ffmin_pair_energy_grad_noalloc.argtypes = [vp, vp, vp, vp, C.c_int32, C.c_double, vp, vp, vp]
     L.ffmin_neighbour_counts.argtypes = [vp, vp, vp]
     L.ffmin_autotune.argtypes = [vp, vp, C.POINTER(C.c_int32)]
+    L.ffmin_set_tuning.argtypes = [vp, C.c_int32, C.c_int32]
+    L.ffmin_get_tuning.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
     L.ffmin_mlp_train.argtypes = [vp, vp, C.c_int64, C.c_int32, C.c_int32, C.c_float, C.c_uint64, vp, vp,
                                   vp, C.POINTER(C.c_float), vp, vp]
     L.ffmin_mlp_work_floats.argtypes = []
@@ -386,6 +390,12 @@ class System:
     def autotune(self, x):
         return ffmin_autotune(self.handle, x)
 
+    def set_tuning(self, density, f32_atoms_per_thread):
+        ffmin_set_tuning(self.handle, density, f32_atoms_per_thread)
+
+    def get_tuning(self):
+        return ffmin_get_tuning(self.handle)
+
 
 def ffmin_status_string(status):
     return lib().ffmin_status_string(int(status)).decode()
@@ -452,7 +462,19 @@ def ffmin_mlp_train(feat, target, steps, batch, lr, seed, w32, adam, work, w16=N
 
 
 def ffmin_autotune(handle, x):
-    """Pick the fastest work-item layout for coordinates x; returns it."""
+    """Pick the fastest work-item layout (and FP32 tile shape) for
+    coordinates x; returns the density."""
     d = C.c_int32()
     _check(lib().ffmin_autotune(C.c_void_p(handle), _dev_ptr(x, ffmin_n_atoms(handle)), C.byref(d)), handle)
     return d.value
+
+
+def ffmin_set_tuning(handle, density, f32_atoms_per_thread):
+    _check(lib().ffmin_set_tuning(C.c_void_p(handle), int(density), int(f32_atoms_per_thread)), handle)
+
+
+def ffmin_get_tuning(handle):
+    """(items per resident block, FP32 i-atoms per thread)"""
+    d, s = C.c_int32(), C.c_int32()
+    _check(lib().ffmin_get_tuning(C.c_void_p(handle), C.byref(d), C.byref(s)), handle)
+    return d.value, s.value

@@ -103,8 +103,9 @@ def gradient(feat, target, w32):
     return work[-N_PARAMS:].cpu().numpy()
 
 
-def minimize_with(systems, w16, precision=ffmin.FFMIN_MIXED, use=True, max_iter=100000):
-    """L-BFGS with (use=True) or without the learned diagonal; returns results."""
+def minimize_with(systems, w16, precision=ffmin.FFMIN_MIXED, use=True, max_iter=100000, **opts):
+    """L-BFGS with (use=True) or without the learned diagonal (further
+    ffmin options by keyword); returns results, seconds and the final x."""
     import torch
     S = ffmin.System(systems, precision)
     if w16 is not None:
@@ -113,7 +114,7 @@ def minimize_with(systems, w16, precision=ffmin.FFMIN_MIXED, use=True, max_iter=
                      device="cuda")
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record()
-    res = S.minimize(x, method="LBFGS", max_iter=max_iter, use_learned_precond=1 if use else 0)
+    res = S.minimize(x, method="LBFGS", max_iter=max_iter, use_learned_precond=1 if use else 0, **opts)
     ev1.record()
     torch.cuda.synchronize()
     S.close()

@@ -108,12 +108,15 @@ def test_batch_other_methods_prefix_fp64(ff, oracle_mod):
             prefix_parity(oracle_mod, s, xg[b], rg[b], kw, ref=ref[b])
 
 
-def test_batch_mixed_minimization_certified(ff, oracle_mod):
-    # 16 systems minimized together in MIXED precision: every result is a
-    # valid stop of the method (the oracle's gradient of the returned point
-    # below 0.1) and reports that point's FP64 energy
+@pytest.mark.parametrize("ipt", [1, 2])
+def test_batch_mixed_minimization_certified(ff, oracle_mod, ipt):
+    # 16 systems minimized together in MIXED precision, with either FP32 tile
+    # shape: every result is a valid stop of the method (the oracle's
+    # gradient of the returned point below 0.1) and reports that point's
+    # FP64 energy
     systems = batch_systems(16, 1500)
     S = ff.System(systems, 1)
+    S.set_tuning(10, ipt)
     x = to_dev([s.x for s in systems])
     rg = S.minimize(x, method=3, max_iter=100000)
     S.close()

@@ -17,7 +17,7 @@ import numpy as np
 import pytest
 
 from paper_1810_03358_gb300 import synth
-from tests.gpu_util import need_gpu, split, to_dev
+from tests.gpu_util import mixed_position_bound, need_gpu, split, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -30,9 +30,12 @@ def ff():
     return need_gpu()
 
 
-def check(ffmin, oracle_mod, systems, prec, xs=None):
+def check(ffmin, oracle_mod, systems, prec, xs=None, tuning=None):
     xs = xs or [s.x for s in systems]
     S = ffmin.System(systems, prec)
+    if tuning is not None:
+        S.set_tuning(*tuning)
+        assert S.get_tuning() == tuple(tuning)
     x = to_dev(xs)
     e, g = S.energy_grad(x)
     e_only = S.energy(x)
@@ -41,7 +44,11 @@ def check(ffmin, oracle_mod, systems, prec, xs=None):
         d, st, go = oracle_mod.energy_terms(s, xs[b], grad=True)
         assert st == 0
         err_e = abs(e[b] - d["total"]) / d["sum_abs"] if d["sum_abs"] > 0 else abs(e[b])
-        assert err_e <= TOL[prec]["e"], (b, err_e)
+        # MIXED: FP32 sums plus the first-order effect of the FP32 rounding
+        # of the positions on the r^-12 terms (tests.gpu_util), which
+        # dominates at the clashing starts' closest pairs
+        tol_e = TOL[prec]["e"] + (mixed_position_bound(xs[b]) if prec == 1 else 0.0)
+        assert err_e <= tol_e, (b, err_e, tol_e)
         if prec == 0:
             assert err_e <= BAR["e"]
         assert abs(e_only[b] - e[b]) <= TOL[prec]["e"] * max(d["sum_abs"], 1.0)
@@ -130,21 +137,43 @@ def test_full_size_30000(ff, oracle_mod, prec):
     S.close()
 
 
+@pytest.mark.parametrize("ipt", [1, 2])
+@pytest.mark.parametrize("density", [1, 3, 20])
+def test_fp32_tile_shapes(ff, oracle_mod, density, ipt):
+    # both FP32 tile shapes (128 threads x 1 i-atom, 64 x 2) at sparse and
+    # dense layouts: a partial tile, ragged tiles and a several-tile system
+    # in one batch, E + grad and energy only within the MIXED bars
+    systems = [synth.make_system(n, 700 + n) for n in (5, 129, 700, 1500)]
+    check(ff, oracle_mod, systems, 1, tuning=(density, ipt))
+
+
+def test_set_tuning_rejects_bad_values(ff):
+    S = ff.System([synth.make_system(50, 3)], 1)
+    for d, ipt in ((0, 2), (21, 2), (10, 0), (10, 3)):
+        with pytest.raises(ff.FfminError):
+            S.set_tuning(d, ipt)
+    assert S.get_tuning() == (10, 2)  # the defaults stay installed
+    S.close()
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_autotuned_layout_keeps_parity(ff, oracle_mod, prec):
-    # the autotuner re-chunks the j range; results stay within the bars
+    # the autotuner re-chunks the j range (and picks the FP32 tile shape);
+    # results stay within the bars
     systems = [synth.make_system(n, 600 + n) for n in (700, 130, 1500)]
     S = ff.System(systems, prec)
     x = to_dev([s.x for s in systems])
     d = S.autotune(x)
     assert d in (3, 6, 10, 20)
+    assert S.get_tuning()[0] == d and S.get_tuning()[1] in ((1, 2) if prec == 1 else (2,))
     e, g = S.energy_grad(x)
     e_only = S.energy(x)
     g = split(g.cpu().numpy(), systems)
     for b, s in enumerate(systems):
         dd, st, go = oracle_mod.energy_terms(s, s.x, grad=True)
-        assert abs(e[b] - dd["total"]) / dd["sum_abs"] <= TOL[prec]["e"]
-        assert abs(e_only[b] - dd["total"]) / dd["sum_abs"] <= TOL[prec]["e"]
+        tol_e = TOL[prec]["e"] + (mixed_position_bound(s.x) if prec == 1 else 0.0)
+        assert abs(e[b] - dd["total"]) / dd["sum_abs"] <= tol_e
+        assert abs(e_only[b] - dd["total"]) / dd["sum_abs"] <= tol_e
         assert np.abs(g[b] - go).max() / np.abs(go).max() <= TOL[prec]["g"]
     if prec == 0:  # the retuned lists drive a minimization: the oracle's steps
         from tests.test_gpu_minimize import prefix_parity

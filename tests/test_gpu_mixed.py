@@ -43,13 +43,15 @@ def unit_antigradient(oracle_mod, s, x):
     return r / np.linalg.norm(r)
 
 
-def check_deltas(ffmin, oracle_mod, systems, xs, rs, hs, blocks=1):
+def check_deltas(ffmin, oracle_mod, systems, xs, rs, hs, blocks=1, tuning=None):
     """GPU differences in both precisions against the oracle; returns the
     worst MIXED error as a fraction of its bar."""
     worst = 0.0
     x = to_dev(xs)
     r = to_dev(rs)
     S64, S32 = ffmin.System(systems, 0), ffmin.System(systems, 1)
+    if tuning is not None:
+        S32.set_tuning(*tuning)
     bars = [BAR_MIXED + mixed_position_bound(x) for x in xs]
     try:
         for h in hs:
@@ -95,12 +97,14 @@ def test_difference_trial_near_minimum(ff, oracle_mod):
     print(f"near minimum: MIXED difference trial error {w:.2f} of its bar")
 
 
-def test_difference_trial_batch(ff, oracle_mod):
-    # a ragged batch of 16 systems (the per-system reduction path)
+@pytest.mark.parametrize("ipt", [1, 2])
+def test_difference_trial_batch(ff, oracle_mod, ipt):
+    # a ragged batch of 16 systems (the per-system reduction path), both
+    # FP32 tile shapes
     sizes = [int(n) for n in synth.batch_sizes(256)[:16]]
     systems = [synth.make_system(min(n, 1200), 1000 + b) for b, n in enumerate(sizes)]
     rs = [unit_antigradient(oracle_mod, s, s.x) for s in systems]
-    check_deltas(ff, oracle_mod, systems, [s.x for s in systems], rs, [1e-3, 0.1])
+    check_deltas(ff, oracle_mod, systems, [s.x for s in systems], rs, [1e-3, 0.1], tuning=(10, ipt))
 
 
 def test_difference_trial_30000(ff, oracle_mod):

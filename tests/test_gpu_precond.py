@@ -42,6 +42,36 @@ def test_identity_network_equals_plain(ff, oracle_mod):
     assert np.array_equal(x0.cpu().numpy(), x1.cpu().numpy())
 
 
+def test_safeguard_window_one_is_plain_lbfgs_on_gpu(ff):
+    # the learned-diagonal safeguard with pc_window = 1 and an unreachable
+    # decrease drops the diagonal after the first (steepest-descent) step:
+    # the FP64 run is the plain run, bit for bit
+    from paper_1810_03358_gb300 import learn
+    s = synth.make_system(60, 42)
+    w16 = (np.random.default_rng(17).normal(scale=0.4, size=449)).astype(np.float16)
+    r0, _, x0 = learn.minimize_with([s], w16, precision=0, use=False, max_iter=40)
+    r1, _, x1 = learn.minimize_with([s], w16, precision=0, use=True, max_iter=40,
+                                    pc_window=1, pc_rel=1e300, pc_gfar=0.0)
+    r2, _, x2 = learn.minimize_with([s], w16, precision=0, use=True, max_iter=40, pc_window=0)
+    assert r0[0]["iterations"] == r1[0]["iterations"] and r0[0]["energy"] == r1[0]["energy"]
+    assert np.array_equal(x0.cpu().numpy(), x1.cpu().numpy())
+    assert not np.array_equal(x0.cpu().numpy(), x2.cpu().numpy())
+
+
+def test_safeguard_prefix_matches_oracle(ff, oracle_mod):
+    # the safeguard firing mid-run (after step 4) on both sides: the same
+    # steps as the oracle's
+    from paper_1810_03358_gb300 import learn
+    s = synth.make_system(80, 43)
+    w16 = (np.random.default_rng(17).normal(scale=0.4, size=449)).astype(np.float16)
+    kw = dict(pc_window=4, pc_rel=1e300, pc_gfar=0.0)
+    r, _, x = learn.minimize_with([s], w16, precision=0, use=True, max_iter=10, **kw)
+    xo, ro = oracle_mod.minimize(s, s.x, method=oracle_mod.LBFGS, max_iter=10,
+                                 mlp_w=w16.astype(np.float64), **kw)
+    assert r[0]["iterations"] == ro["iterations"] and r[0]["energy_evals"] == ro["energy_evals"]
+    assert abs(r[0]["energy"] - ro["energy"]) <= 1e-5 * abs(ro["energy"])
+
+
 def test_preconditioned_prefix_matches_oracle(ff, oracle_mod):
     from paper_1810_03358_gb300 import learn
     s = synth.make_system(80, 43)

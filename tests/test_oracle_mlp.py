@@ -64,3 +64,48 @@ def test_scaled_network_changes_lbfgs(oracle_mod):
     # two-loop step only in exact arithmetic up to history effects; the runs
     # must both be valid descents
     assert r2["energy"] < oracle_mod.energy(s, s.x)
+
+
+def _varied_network():
+    # per-atom diagonals well away from 1 (a network of random weights)
+    w = np.random.default_rng(17).normal(scale=0.4, size=449)
+    return w
+
+
+def test_safeguard_window_one_is_plain_lbfgs(oracle_mod):
+    # pc_window = 1 with an unreachable decrease (pc_rel huge) and no
+    # gradient floor: the check after the first step (a steepest-descent
+    # step, taken before any learned direction) drops the diagonal, so the
+    # whole run is plain L-BFGS, bit for bit
+    s = synth.make_system(40, 41)
+    w = _varied_network()
+    x1, r1 = oracle_mod.minimize(s, s.x, method=oracle_mod.LBFGS, max_iter=60)
+    x2, r2 = oracle_mod.minimize(s, s.x, method=oracle_mod.LBFGS, max_iter=60, mlp_w=w,
+                                 pc_window=1, pc_rel=1e300, pc_gfar=0.0)
+    assert r1["iterations"] == r2["iterations"] and r1["energy"] == r2["energy"]
+    assert np.array_equal(x1, x2)
+    # the network does change the run when the safeguard is off
+    x3, r3 = oracle_mod.minimize(s, s.x, method=oracle_mod.LBFGS, max_iter=60, mlp_w=w, pc_window=0)
+    assert not np.array_equal(x1, x3)
+
+
+def test_safeguard_keeps_the_diagonal_while_the_energy_falls(oracle_mod):
+    # every 5 steps the energy falls by far more than 1e-12 |E| on a clashing
+    # start: the safeguard never fires and the run is the unguarded one
+    s = synth.make_system(40, 41)
+    w = _varied_network()
+    x1, r1 = oracle_mod.minimize(s, s.x, method=oracle_mod.LBFGS, max_iter=60, mlp_w=w, pc_window=0)
+    x2, r2 = oracle_mod.minimize(s, s.x, method=oracle_mod.LBFGS, max_iter=60, mlp_w=w,
+                                 pc_window=5, pc_rel=1e-12, pc_gfar=0.0)
+    assert r1["energy"] == r2["energy"] and np.array_equal(x1, x2)
+
+
+def test_safeguard_needs_a_gradient_far_from_the_tolerance(oracle_mod):
+    # the same unreachable decrease, but |grad|_inf must exceed 1e300 times
+    # the tolerance: never true, so the diagonal stays in use
+    s = synth.make_system(40, 41)
+    w = _varied_network()
+    x1, r1 = oracle_mod.minimize(s, s.x, method=oracle_mod.LBFGS, max_iter=60, mlp_w=w, pc_window=0)
+    x2, r2 = oracle_mod.minimize(s, s.x, method=oracle_mod.LBFGS, max_iter=60, mlp_w=w,
+                                 pc_window=1, pc_rel=1e300, pc_gfar=1e300)
+    assert r1["energy"] == r2["energy"] and np.array_equal(x1, x2)
