@@ -407,6 +407,7 @@ def minimizations(args, ffmin, synth, torch, dev, rank=0, ws=1):
         x = torch.tensor(np.concatenate([q.x.reshape(-1) for q in systems]), dtype=torch.float64, device=dev)
         if tune:
             S.autotune(x)
+        tuning = S.get_tuning()
         S.minimize(x.clone(), method="LBFGS", max_iter=2, use_learned_precond=int(learned))  # warm-up
         torch.cuda.synchronize()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -427,6 +428,9 @@ def minimizations(args, ffmin, synth, torch, dev, rank=0, ws=1):
                 "max_final_grad_inf": max(q["grad_inf"] for q in r),
                 "iterations_max": max(q["iterations"] for q in r),
                 "iterations_sum": sum(q["iterations"] for q in r),
+                "fp64_phase_iterations_max": max(q["fp64_iterations"] for q in r),
+                "not_converged": [b for b, q in enumerate(r) if q["status_name"] != "ok"],
+                "tuning": {"items_per_block": tuning[0], "f32_atoms_per_thread": tuning[1]},
                 "pair_interactions_per_s": st["pair_interactions"] / t, "gpu_launches": st["launches"]}
 
     def ratio(a, b):
