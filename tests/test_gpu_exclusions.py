@@ -69,9 +69,11 @@ def test_energy_gradient(ff, oracle_mod, n):
     check(ff, oracle_mod, [excl(synth.make_system(n, 600 + n))], 0)
 
 
-def check_mixed(ffmin, oracle_mod, systems, xs=None):
+def check_mixed(ffmin, oracle_mod, systems, xs=None, tuning=None):
     xs = xs or [s.x for s in systems]
     S = ffmin.System(systems, 1)
+    if tuning is not None:
+        S.set_tuning(*tuning)
     x = to_dev(xs)
     e, g = S.energy_grad(x)
     e_only = S.energy(x)
@@ -91,6 +93,14 @@ def check_mixed(ffmin, oracle_mod, systems, xs=None):
 @pytest.mark.parametrize("n", [3, 4, 64, 129, 300, 1000])
 def test_mixed_energy_gradient(ff, oracle_mod, n):
     check_mixed(ff, oracle_mod, [excl(synth.make_system(n, 600 + n))])
+
+
+@pytest.mark.parametrize("ipt", [1, 2])
+def test_mixed_tile_shapes(ff, oracle_mod, ipt):
+    # the masked FP32 sweeps in both tile shapes (one or two i-atoms per
+    # thread), a partial tile and a several-tile system in one batch
+    systems = [excl(synth.make_system(n, 640 + n)) for n in (70, 400, 1000)]
+    check_mixed(ff, oracle_mod, systems, tuning=(10, ipt))
 
 
 def test_mixed_batch_and_minimized_geometry(ff, oracle_mod):
